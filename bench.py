@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Throughput of the porous lattice Boltzmann time step on one GB300.
+
+Workload (default): the shale matrix with fractures, 4096 x 4096 D2Q9
+lattice, matrix eps ~ U(0.05, 0.1), log10 k_i ~ N(-6, 0.3), 40 straight
+fractures (eps 0.9, k_i 1e-2), Kn from the local pressure (0.5 at the
+inlet), pressure-driven in x (rho 1.0005 -> 0.9995), periodic in y,
+tau 0.8, Forchheimer drag on.  FP32-stored populations are the headline;
+the FP16-stored run is reported beside it.
+
+One JSON line on rank 0:
+  value     lattice updates per second (GLUPS) of ``lbmp_step`` with the
+            lattice resident in HBM (1.3 GB FP32 working set >> 129 MB L2)
+  e2e       the same metric through the public API from host buffers:
+            lbmp_set_fields from host arrays + K steps + lbmp_permeability
+  roofline  the fused step kernel against the measured HBM copy bandwidth
+  cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample
+
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
+With torchrun and N > 1 ranks every rank runs an independent replica (the
+step needs no exchange between replicas); the value is the sum of their
+lattice updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 porous-LBM GLUPS & %HBM peak, FP32 vs FP16-stored at <=1e-3 k_a err"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32",
+                    help="storage of the headline value; the other one is reported beside it")
+    ap.add_argument("--no-other", action="store_true", help="skip the second storage run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(size: int):
+    from paper_1411_7051_gb300 import media
+    med = media.shale_fractures(n=size, seed=3, n_fractures=40 if size >= 1024 else 4,
+                                length=(200.0, 2000.0) if size >= 2048 else
+                                (size / 20, size / 2))
+    cfg = dict(nx=size, ny=size, tau=0.8, bc_x=1, bc_y=0, rho_in=1.0005, rho_out=0.9995,
+               forchheimer=1)
+    return med, cfg
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(kernel_tag: str, source_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when
+    the summary was taken on a different build of the kernels."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(kernel_tag)
+    if not e or e.get("source_hash") != source_hash:
+        return None
+    return e
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                 power=float(parts[3]) if parts[3] not in ("[N/A]", "") else None,
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            if r["hw"] == "Active":
+                reasons.add("hw_slowdown")
+            if r["hwt"] == "Active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"] == "Active":
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"] == "Active":
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU (oracle)
+def oracle_rate(med, cfg, seconds: float, crop: int = 1024):
+    """FP64 oracle lattice updates per second on a crop of the workload."""
+    from oracle import oracle
+    n = min(crop, cfg["nx"])
+    sub = med.crop(n, n)
+    p = oracle.make_params(n, n, tau=cfg["tau"], bc_x=cfg["bc_x"], bc_y=cfg["bc_y"],
+                           rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
+                           forchheimer=cfg["forchheimer"])
+    sim = oracle.OracleSim(p)
+    sim.set_fields(sub.eps, sub.k_i, sub.kn)
+    sim.step(1)
+    t0 = time.perf_counter()
+    sim.step(1)
+    per = time.perf_counter() - t0
+    steps = max(2, int(seconds / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt, steps, n, oracle.max_threads()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    med, cfg = workload(args.size)
+    from oracle import oracle
+    n = min(1024, args.size)
+    sub = med.crop(n, n)
+    p = oracle.make_params(n, n, tau=cfg["tau"], bc_x=cfg["bc_x"], bc_y=cfg["bc_y"],
+                           rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
+                           forchheimer=cfg["forchheimer"])
+    sim = oracle.OracleSim(p)
+    sim.set_fields(sub.eps, sub.k_i, sub.kn)
+    sim.step(max(3, args.warmup))
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    glups = n * n * args.steps / dt / 1e9
+    sample = f"{n}x{n} crop of the {args.size}x{args.size} workload, {args.steps} steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, cfg, "fp64 oracle (CPU)"),
+        "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, cfg, storage):
+    return {"workload": f"shale matrix with 40 fractures, {args.size}x{args.size} D2Q9, "
+                        "pressure-driven x, periodic y, Forchheimer on",
+            "nx": cfg["nx"], "ny": cfg["ny"], "tau": cfg["tau"], "storage": storage,
+            "l2": "inputs larger than L2 (working set > 129 MB), no flush"}
+
+
+# ------------------------------------------------------------- GPU (ours)
+def time_storage(lbmp, torch, med, cfg, storage, K, W):
+    st = lbmp.STORE_FP32 if storage == "fp32" else lbmp.STORE_FP16
+    sc = lbmp.SimConfig(cfg["nx"], cfg["ny"], tau=cfg["tau"], bc_x=cfg["bc_x"],
+                        bc_y=cfg["bc_y"], rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
+                        forchheimer=cfg["forchheimer"], storage=st)
+    sim = lbmp.Sim(sc)
+    sim.set_fields(med.eps, med.k_i, med.kn)
+    sim.step(W)
+    sim.synchronize()
+    info0 = sim.info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(sim.stream)
+    sim.step(K)
+    e1.record(sim.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    info1 = sim.info()
+    kg, um = sim.permeability()
+    out = dict(ms=ms, launches=int(info1.launches - info0.launches),
+               nodes=int(info1.fluid_nodes), bpu=float(info1.bytes_per_update),
+               scale=float(info1.fp16_scale), k_g=kg)
+    sim.close()
+    return out
+
+
+def time_e2e(lbmp, torch, med, cfg, K):
+    sc = lbmp.SimConfig(cfg["nx"], cfg["ny"], tau=cfg["tau"], bc_x=cfg["bc_x"],
+                        bc_y=cfg["bc_y"], rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
+                        forchheimer=cfg["forchheimer"], storage=lbmp.STORE_FP32)
+    sim = lbmp.Sim(sc)
+    import numpy as np
+    eps = np.ascontiguousarray(med.eps)
+    k_i = np.ascontiguousarray(med.k_i)
+    kn = np.ascontiguousarray(med.kn)
+    sim.set_fields(eps, k_i, kn)  # warm the allocator and the graphs
+    sim.step(64)
+    sim.permeability()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_fields(eps, k_i, kn)
+    sim.step(K)
+    kg, _ = sim.permeability()
+    dt = time.perf_counter() - t0
+    sim.close()
+    n = cfg["nx"] * cfg["ny"]
+    return dict(s=dt, h2d=3 * 8 * n, d2h=6 * 8 + 4)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1411_7051_gb300 import build as lbuild, lbmp
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the product path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl")
+    lbmp.load()
+    K, W = args.steps, max(3, args.warmup)
+    med, cfg = workload(args.size)
+    primary = args.storage
+    other = "fp16" if primary == "fp32" else "fp32"
+
+    with ClockSampler(local) as clk:
+        res = time_storage(lbmp, torch, med, cfg, primary, K, W)
+    clocks = clk.summary()
+    res_other = None
+    if not args.no_other:
+        res_other = time_storage(lbmp, torch, med, cfg, other, K, W)
+    e2e = None if args.no_e2e else time_e2e(lbmp, torch, med, cfg, K)
+
+    # slowest rank decides
+    ms = res["ms"]
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        if e2e:
+            t = torch.tensor([e2e["s"]], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e["s"] = float(t.item())
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    nodes = res["nodes"]
+    glups = ws * nodes * K / (ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    src = lbuild.source_hash()
+
+    def roofline(r, tag):
+        per_launch_s = r["ms"] * 1e-3 / K          # one step kernel per time step
+        alg = r["bpu"] * r["nodes"]                 # algorithmic bytes per launch
+        achieved = alg / per_launch_s / 1e9
+        tr = profiled_traffic(tag, src)
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                "bytes_per_update": r["bpu"],
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                "traffic_per_update": (tr["dram_bytes_per_launch"] / r["nodes"] if tr else None),
+                "kernel": f"lbmp::step_kernel<{tag}>"}
+
+    line = {
+        "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(args, cfg, primary),
+        "roofline": roofline(res, "StoreF32" if primary == "fp32" else "StoreF16"),
+        "gpu_launches": res["launches"],
+        "clocks": clocks,
+        "k_g": res["k_g"],
+    }
+    if res_other:
+        g2 = ws * res_other["nodes"] * K / (res_other["ms"] * 1e-3) / 1e9
+        line[f"{other}_stored"] = {
+            "value": g2, "unit": "GLUPS", "ms_per_step": res_other["ms"] / K,
+            "ratio_fp16_over_fp32": (g2 / glups) if other == "fp16" else (glups / g2),
+            "roofline": roofline(res_other, "StoreF32" if other == "fp32" else "StoreF16"),
+            "fp16_scale": res_other["scale"], "k_g": res_other["k_g"],
+        }
+    if e2e:
+        line["e2e"] = {"value": ws * nodes * K / e2e["s"] / 1e9, "unit": "GLUPS",
+                       "h2d_bytes_per_step": e2e["h2d"] / K, "d2h_bytes_per_step": e2e["d2h"] / K,
+                       "what": "lbmp_set_fields from host float64 arrays + K steps + "
+                               "lbmp_permeability to host, wall clock"}
+    if not args.no_cpu and ws == 1:
+        rate, steps, n, cores = oracle_rate(med, cfg, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "GLUPS", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{n}x{n} crop of the workload, {steps} FP64 steps"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

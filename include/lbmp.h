@@ -1,0 +1,173 @@
+/*
+ * lbmp — GB300-native time step of the generalized lattice Boltzmann model
+ * for flow through tight porous media with Klinkenberg's effect
+ * (Chen, Fang, Kang, Hyman, Viswanathan, Tao, arXiv:1411.7051).
+ *
+ * C ABI.  Plain pointers and sizes; no C++ or framework types cross it.
+ * Every entry point returns an lbmp_status; no exception escapes.  On an
+ * error the thread-local message of lbmp_last_error() says what failed.
+ *
+ * Model (Section III): D2Q9 (Eq. 13), BGK evolution (Eq. 12) with the
+ * porosity-weighted equilibrium (Eq. 14), Guo's forcing term (Eq. 15, last
+ * term taken over eps so that sum_i F_i = 0), density and velocity from
+ * Eq. 16-17 (the quadratic form when the Forchheimer drag of Eq. 2 is kept),
+ * total force Eq. 2 / Eq. 8, and the apparent permeability k_a = k_i f_c(Kn)
+ * of Eq. 3 with the Beskok-Karniadakis-Civan factor of Eq. 6-7 (b = -1).
+ * Lattice units: dt = dx = 1, c = 1, c_s^2 = 1/3, nu_e = (tau - 1/2)/3,
+ * nu = nu_e / J.
+ *
+ * Array conventions: node fields are row-major [ny][nx] (x fastest) float64;
+ * populations are plane-major [9][ny][nx] float64 in the order of Eq. 13:
+ * e_0 = (0,0), e_1..e_4 = (1,0), (0,1), (-1,0), (0,-1),
+ * e_5..e_8 = (1,1), (-1,1), (-1,-1), (1,-1).
+ * The caller owns every pointer it passes; the library copies what it needs
+ * and owns every device buffer it allocates.  `where` says whether a caller
+ * pointer is host (LBMP_HOST) or device (LBMP_DEVICE) memory of the
+ * context's GPU.
+ */
+#ifndef LBMP_H
+#define LBMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lbmp_status;
+#define LBMP_OK 0
+#define LBMP_EINVAL 1   /* invalid argument or field value */
+#define LBMP_ENOMEM 2   /* device or host allocation failed */
+#define LBMP_ECUDA 3    /* a CUDA call failed (no device, launch error ...) */
+#define LBMP_ESTATE 4   /* call out of order (e.g. step before set_fields) */
+#define LBMP_ENAN 5     /* a reduction met a non-finite velocity or density */
+#define LBMP_ETIMEOUT 6 /* a bounded device wait gave up */
+
+/* boundary kinds */
+#define LBMP_BCX_PERIODIC 0
+#define LBMP_BCX_PRESSURE 1 /* density imposed at x = 0 and x = nx-1 */
+#define LBMP_BCY_PERIODIC 0
+#define LBMP_BCY_WALLS 1 /* rows 0 and ny-1 are solid plates */
+
+/* population storage in device memory (arithmetic is FP32 in both) */
+#define LBMP_STORE_FP32 0 /* f_i - w_i rho0 as float */
+#define LBMP_STORE_FP16 1 /* (f_i - w_i rho0) * S as IEEE half, S = 2^s */
+
+#define LBMP_HOST 0
+#define LBMP_DEVICE 1
+
+typedef struct lbmp_params {
+  int32_t nx, ny;       /* lattice size; nx, ny >= 1 */
+  double tau;           /* relaxation time of Eq. 12, > 0.5 */
+  double J;             /* viscosity ratio nu_e / nu of Eq. 1b (paper: 1); 0 means 1 */
+  double Gx, Gy;        /* external body force G of Eq. 2 */
+  int32_t bc_x;         /* LBMP_BCX_*; PRESSURE needs nx >= 3 */
+  int32_t bc_y;         /* LBMP_BCY_*; WALLS needs ny >= 3 */
+  double rho0;          /* initial density; also the storage shift; 0 means 1 */
+  double rho_in;        /* density imposed at x = 0 (PRESSURE only) */
+  double rho_out;       /* density imposed at x = nx-1 (PRESSURE only) */
+  int32_t forchheimer;  /* 1: Eq. 2 with F_eps = 1.75/sqrt(150 eps^3); 0: Eq. 8 */
+  int32_t storage;      /* LBMP_STORE_* */
+  int32_t fp16_log2_scale; /* s of S = 2^s for FP16 storage; 0 = automatic */
+  int32_t reserved;     /* must be 0 */
+  void *stream;         /* cudaStream_t for all work; NULL = a private stream */
+} lbmp_params;
+
+typedef struct lbmp_info {
+  int32_t nx, ny;
+  int32_t pitch;          /* padded row length (elements) of device planes */
+  int32_t storage;
+  int64_t fluid_nodes;    /* lattice updates per time step */
+  int64_t steps;          /* time level of the current state */
+  double bytes_per_update;/* algorithmic HBM bytes per lattice update */
+  double fp16_scale;      /* S (1 for FP32 storage) */
+  double eps_mean;        /* mean porosity of the fluid nodes */
+  int64_t device_bytes;   /* device memory held by the context */
+  int64_t launches;       /* kernels launched by this context so far */
+} lbmp_info;
+
+typedef struct lbmp_ctx lbmp_ctx;
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *lbmp_last_error(void);
+
+/* Create a context on the current CUDA device: validates p, allocates the
+ * two population buffers, the per-node medium and the reduction scratch.
+ * Errors: EINVAL (bad parameters; nothing allocated), ENOMEM, ECUDA.
+ * Section III (Eq. 12-17) defines the state the context holds. */
+lbmp_status lbmp_create(const lbmp_params *p, lbmp_ctx **out);
+
+/* Free every resource of ctx.  NULL is accepted. */
+lbmp_status lbmp_destroy(lbmp_ctx *ctx);
+
+/* Set the medium and restart from rest.  eps: porosity in [0, 1] (0 =
+ * impermeable node, Section III); k_i: intrinsic permeability > 0 or +inf
+ * (open pore); kn: Knudsen number >= 0, finite.  All [ny][nx] float64.
+ * Stores per node eps and 1 / k_a with k_a = k_i f_c(Kn) (Eq. 3, 6-7), and
+ * sets every population to w_i rho0.  Values of wall rows are ignored.
+ * Errors: EINVAL (a value out of range, or k_a < 1e-15; the context then
+ * holds no valid medium until the next successful call), ECUDA. */
+lbmp_status lbmp_set_fields(lbmp_ctx *ctx, const double *eps, const double *k_i,
+                            const double *kn, int32_t where);
+
+/* Advance n >= 0 time steps of Eq. 12 (collide and stream, walls, periodic
+ * edges and pressure columns fused).  Asynchronous on the context stream.
+ * Errors: EINVAL (n < 0), ESTATE (no fields set), ECUDA. */
+lbmp_status lbmp_step(lbmp_ctx *ctx, int64_t n);
+
+/* Wait for all work queued on the context stream. */
+lbmp_status lbmp_synchronize(lbmp_ctx *ctx);
+
+/* Density (Eq. 16a) and velocity (Eq. 17, or its quadratic form) of the
+ * current time level, [ny][nx] float64 each; wall rows read 0.  Any output
+ * pointer may be NULL.  Synchronous. */
+lbmp_status lbmp_macroscopic(lbmp_ctx *ctx, double *rho, double *ux, double *uy,
+                             int32_t where);
+
+/* Post-stream populations f_i(x, t) of the current time level,
+ * [9][ny][nx] float64; wall rows read 0.  Synchronous. */
+lbmp_status lbmp_populations(lbmp_ctx *ctx, double *f, int32_t where);
+
+/* Replace the current post-stream populations by f ([9][ny][nx] float64;
+ * wall rows ignored).  With LBMP_BCX_PRESSURE columns 0 and nx-1 are then
+ * re-extrapolated from their neighbours, as at every time level.  FP16
+ * storage rounds the values.  Synchronous. */
+lbmp_status lbmp_set_populations(lbmp_ctx *ctx, const double *f, int32_t where);
+
+/* Global permeability by Darcy's law over the whole domain (Section IV.A,
+ * discussion of Fig. 3): k_g = nu <u_x> / G_eff, <u_x> the mean velocity of
+ * all fluid nodes, G_eff = G_x + c_s^2 (rho_in - rho_out) / (eps_mean rho0
+ * (nx - 1)) (the pressure term only with LBMP_BCX_PRESSURE; eps p = c_s^2
+ * rho, Eq. 1b).  FP64 reduction, deterministic order.  Synchronous.
+ * Errors: ENAN (a non-finite velocity), ECUDA. */
+lbmp_status lbmp_permeability(lbmp_ctx *ctx, double *k_g, double *u_mean);
+
+/* Relative velocity residual ||u - u_prev||_2 / ||u||_2 over fluid nodes,
+ * u_prev being the velocity at the previous lbmp_residual call (zero after
+ * set_fields); then stores u as the new u_prev.  FP64.  Synchronous. */
+lbmp_status lbmp_residual(lbmp_ctx *ctx, double *r);
+
+/* Total mass sum(rho) over fluid nodes, FP64.  Synchronous. */
+lbmp_status lbmp_mass(lbmp_ctx *ctx, double *m);
+
+/* Eq. 6-7 correction factor f_c(Kn), b = -1, f_c(0) = 1.  Host function;
+ * returns NaN for Kn < 0 or NaN. */
+double lbmp_fc(double kn);
+
+/* Checkpoint: bytes of a state blob (header + raw population buffer). */
+lbmp_status lbmp_state_size(lbmp_ctx *ctx, size_t *bytes);
+/* Copy the current state into buf (bytes >= lbmp_state_size).  Synchronous. */
+lbmp_status lbmp_get_state(lbmp_ctx *ctx, void *buf, size_t bytes, int32_t where);
+/* Restore a state written by lbmp_get_state of a context with the same
+ * nx, ny and storage.  Errors: EINVAL (size or header mismatch). */
+lbmp_status lbmp_set_state(lbmp_ctx *ctx, const void *buf, size_t bytes, int32_t where);
+
+/* Sizes, storage and counters of ctx. */
+lbmp_status lbmp_get_info(lbmp_ctx *ctx, lbmp_info *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMP_H */

@@ -341,11 +341,13 @@ void orc_get_populations(const orc_sim *s, double *out) {
     for (int i = 0; i < 9; ++i) out[(int64_t)i * n + j] = s->f[j * 9 + i];
 }
 
-/* Overwrite the post-stream populations ([9][ny][nx]). */
+/* Overwrite the post-stream populations ([9][ny][nx]).  The result is a
+ * time level, so the pressure columns are extrapolated again. */
 void orc_set_populations(orc_sim *s, const double *in) {
   int64_t n = (int64_t)s->p.nx * s->p.ny;
   for (int64_t j = 0; j < n; ++j)
     for (int i = 0; i < 9; ++i) s->f[j * 9 + i] = in[(int64_t)i * n + j];
+  orc_apply_pressure(s);
 }
 
 /* rho and the physical velocity (Eq. 16a, 17) of every node; wall rows

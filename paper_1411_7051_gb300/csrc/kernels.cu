@@ -1,0 +1,286 @@
+// CUDA kernels of the porous lattice Boltzmann step for sm_103a
+// (Chen et al., arXiv:1411.7051, Section III).
+//
+// The step is a stencil stream: every population is read once and written
+// once per time step, so the roofline is HBM bandwidth (no dense
+// contraction, no tensor cores).  One fused kernel pulls the nine
+// populations of a node (periodic wrap, halfway bounce-back at plates,
+// pressure-column extrapolation), solves Eq. 16-17 for the velocity, forms
+// Eq. 2, Eq. 14 and Eq. 15 and writes the nine post-collision values.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+#include "lattice.cuh"
+
+namespace lbmp {
+
+constexpr int kStepBX = 128;   // threads per block along x
+constexpr int kStepNPT = 2;    // nodes per thread (strided by kStepBX)
+constexpr int kMacroBX = 256;
+constexpr int kMediumBX = 256;
+
+// ------------------------------------------------------------- step kernel
+template <class S, int NPT>
+__global__ void __launch_bounds__(kStepBX)
+    step_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
+                typename S::T *__restrict__ fout, const float2 *__restrict__ med) {
+  const int y = a.y0 + blockIdx.y;
+  const int xb = blockIdx.x * (kStepBX * NPT) + threadIdx.x;
+  const long long row = (long long)y * a.pitch;
+  float d[NPT][9];
+  float2 m[NPT];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    const int x = xb + k * kStepBX;
+    if (x < a.nx) {
+      pull_node<S>(fin, a, x, y, d[k]);
+      m[k] = med[row + x];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    const int x = xb + k * kStepBX;
+    if (x >= a.nx) continue;
+    if (a.pressure && (x == 0 || x == a.nx - 1))
+      pressure_node<S>(fin, med, a, x, y, m[k].x, d[k]);
+    const NodeState s = node_state(d[k], m[k].x, m[k].y, a);
+    collide(d[k], s, m[k].x, a);
+    typename S::T *o = fout + row + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) S::st(o + i * a.plane, d[k][i], a.scale);
+  }
+}
+
+cudaError_t launch_step(int storage, const StepArgs &a, int rows, const void *fin,
+                        void *fout, const float2 *med, cudaStream_t s) {
+  if (rows <= 0 || a.nx <= 0) return cudaSuccess;
+  dim3 block(kStepBX);
+  dim3 grid((a.nx + kStepBX * kStepNPT - 1) / (kStepBX * kStepNPT), rows);
+  if (storage == 0)
+    step_kernel<StoreF32, kStepNPT><<<grid, block, 0, s>>>(
+        a, (const float *)fin, (float *)fout, med);
+  else
+    step_kernel<StoreF16, kStepNPT><<<grid, block, 0, s>>>(
+        a, (const __half *)fin, (__half *)fout, med);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- block reduction helper
+// Sums kNQ doubles over the block in a fixed order and writes them to
+// partials[blockLinear * kNQ + q] (deterministic for a fixed launch shape).
+template <int BX>
+__device__ __forceinline__ void block_reduce_store(double v[kNQ], double *partials) {
+  __shared__ double red[BX / 32][kNQ];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) {
+    double t = v[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if (lane == 0) red[warp][q] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNQ) {
+    double t = 0.0;
+    for (int w = 0; w < BX / 32; ++w) t += red[w][threadIdx.x];
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    partials[b * kNQ + threadIdx.x] = t;
+  }
+}
+
+// ------------------------------------------- macroscopic / reduction kernel
+template <class S>
+__global__ void __launch_bounds__(kMacroBX)
+    macro_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
+                 const float2 *__restrict__ med, const MacroOut o) {
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * kMacroBX + threadIdx.x;
+  const bool wall = a.walls && (y == 0 || y == a.ny - 1);
+  const long long n = (long long)a.nx * a.ny;
+  const long long j = (long long)y * a.nx + x;
+  double v[kNQ] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (x < a.nx) {
+    if (wall) {
+      if (o.rho) o.rho[j] = 0.0;
+      if (o.ux) o.ux[j] = 0.0;
+      if (o.uy) o.uy[j] = 0.0;
+      if (o.pops)
+        for (int i = 0; i < 9; ++i) o.pops[i * n + j] = 0.0;
+    } else {
+      float d[9];
+      const float2 m = med[(long long)y * a.pitch + x];
+      pull_node<S>(fin, a, x, y, d);
+      if (a.pressure && (x == 0 || x == a.nx - 1)) pressure_node<S>(fin, med, a, x, y, m.x, d);
+      const NodeState s = node_state(d, m.x, m.y, a);
+      if (o.rho) o.rho[j] = (double)s.rho;
+      if (o.ux) o.ux[j] = (double)s.ux;
+      if (o.uy) o.uy[j] = (double)s.uy;
+      if (o.pops) {
+        const double r0 = (double)a.rho0;
+        const double w[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+        for (int i = 0; i < 9; ++i) o.pops[i * n + j] = w[i] * r0 + (double)d[i];
+      }
+      if (o.partials) {
+        const double ux = s.ux, uy = s.uy;
+        const bool finite = isfinite(s.ux) && isfinite(s.uy) && isfinite(s.rho);
+        v[0] = finite ? ux : 0.0;
+        v[1] = finite ? uy : 0.0;
+        v[2] = finite ? (double)s.drho : 0.0;
+        v[3] = finite ? ux * ux + uy * uy : 0.0;
+        if (o.uprev) {
+          const long long jp = (long long)y * a.pitch + x;
+          const float2 up = o.uprev[jp];
+          const double dx = ux - (double)up.x, dy = uy - (double)up.y;
+          v[4] = finite ? dx * dx + dy * dy : 0.0;
+          if (o.update_prev) o.uprev[jp] = make_float2(s.ux, s.uy);
+        }
+        v[5] = finite ? 0.0 : 1.0;
+      }
+    }
+  }
+  if (o.partials) block_reduce_store<kMacroBX>(v, o.partials);
+}
+
+int macro_blocks(const StepArgs &a) {
+  return ((a.nx + kMacroBX - 1) / kMacroBX) * a.ny;
+}
+
+cudaError_t launch_macro(int storage, const StepArgs &a, const void *fin,
+                         const float2 *med, const MacroOut &o, cudaStream_t s) {
+  dim3 block(kMacroBX);
+  dim3 grid((a.nx + kMacroBX - 1) / kMacroBX, a.ny);
+  if (storage == 0)
+    macro_kernel<StoreF32><<<grid, block, 0, s>>>(a, (const float *)fin, med, o);
+  else
+    macro_kernel<StoreF16><<<grid, block, 0, s>>>(a, (const __half *)fin, med, o);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- finalize
+constexpr int kFinBX = 256;
+
+__global__ void __launch_bounds__(kFinBX)
+    finalize_kernel(const double *__restrict__ partials, int nblocks, int nq,
+                    double *__restrict__ out) {
+  __shared__ double sh[kFinBX];
+  for (int q = 0; q < nq; ++q) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kFinBX) t += partials[(long long)b * nq + q];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = kFinBX / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sh[0];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_finalize(const double *partials, int nblocks, int nq, double *out,
+                            cudaStream_t s) {
+  finalize_kernel<<<1, kFinBX, 0, s>>>(partials, nblocks, nq, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- medium
+__global__ void __launch_bounds__(kMediumBX)
+    medium_kernel(const double *__restrict__ eps, const double *__restrict__ k_i,
+                  const double *__restrict__ kn, int nx, int ny, int pitch, int y_lo,
+                  int y_hi, float2 *__restrict__ med, unsigned *bad,
+                  double *__restrict__ partials) {
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * kMediumBX + threadIdx.x;
+  double v[kNQ] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (x < nx) {
+    const long long j = (long long)y * nx + x;
+    float2 out = make_float2(0.0f, 0.0f);
+    if (y >= y_lo && y < y_hi) {
+      const double e = eps[j], k = k_i[j], K = kn[j];
+      unsigned flags = 0;
+      if (!(e >= 0.0 && e <= 1.0)) flags |= 1u;               // also NaN
+      if (!(k > 0.0)) flags |= 2u;                             // NaN, <= 0
+      if (!(K >= 0.0 && isfinite(K))) flags |= 4u;
+      double inv_k = 0.0;
+      if (!flags) {
+        const double ka = k * fc_bkc(K);                       // Eq. 3, 6-7
+        if (!(ka >= 1e-15)) flags |= 8u;                       // 1/k_a must fit FP32 math
+        inv_k = isinf(ka) ? 0.0 : 1.0 / ka;
+      }
+      if (flags) atomicOr(bad, flags);
+      out = make_float2((float)e, (float)inv_k);
+      v[0] = e;
+      v[1] = 1.0;
+    }
+    med[(long long)y * pitch + x] = out;
+  }
+  block_reduce_store<kMediumBX>(v, partials);
+}
+
+int medium_blocks(int nx, int ny) { return ((nx + kMediumBX - 1) / kMediumBX) * ny; }
+
+cudaError_t launch_medium(const double *eps, const double *k_i, const double *kn,
+                          int nx, int ny, int pitch, int y_lo, int y_hi, float2 *med,
+                          unsigned *bad, double *partials, cudaStream_t s) {
+  dim3 block(kMediumBX);
+  dim3 grid((nx + kMediumBX - 1) / kMediumBX, ny);
+  medium_kernel<<<grid, block, 0, s>>>(eps, k_i, kn, nx, ny, pitch, y_lo, y_hi, med, bad,
+                                       partials);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------- population loading
+// B_j(z) = f_j(z + e_j) when z + e_j is a fluid node (wrapped), f_opp(j)(z)
+// when it lies in a plate row, and 0 (unused) beyond a pressure column.
+template <class S>
+__global__ void __launch_bounds__(kMacroBX)
+    load_pops_kernel(const StepArgs a, const double *__restrict__ f,
+                     typename S::T *__restrict__ buf) {
+  const int y = a.y0 + blockIdx.y;
+  const int x = blockIdx.x * kMacroBX + threadIdx.x;
+  if (x >= a.nx) return;
+  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  const double w[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                       1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+  const long long n = (long long)a.nx * a.ny;
+  const double r0 = (double)a.rho0;
+  for (int j = 0; j < 9; ++j) {
+    int tx = x + ex[j], ty = y + ey[j];
+    double val;
+    if (a.walls && (ty == 0 || ty == a.ny - 1)) {
+      val = f[opp[j] * n + (long long)y * a.nx + x];
+    } else {
+      ty = (ty + a.ny) % a.ny;
+      if (tx < 0 || tx >= a.nx) {
+        if (a.pressure) {
+          val = w[j] * r0;
+        } else {
+          tx = (tx + a.nx) % a.nx;
+          val = f[j * n + (long long)ty * a.nx + tx];
+        }
+      } else {
+        val = f[j * n + (long long)ty * a.nx + tx];
+      }
+    }
+    S::st(buf + j * a.plane + (long long)y * a.pitch + x, (float)(val - w[j] * r0),
+          a.scale);
+  }
+}
+
+cudaError_t launch_load_pops(int storage, const StepArgs &a, int rows, const double *f,
+                             void *buf, cudaStream_t s) {
+  dim3 block(kMacroBX);
+  dim3 grid((a.nx + kMacroBX - 1) / kMacroBX, rows);
+  if (storage == 0)
+    load_pops_kernel<StoreF32><<<grid, block, 0, s>>>(a, f, (float *)buf);
+  else
+    load_pops_kernel<StoreF16><<<grid, block, 0, s>>>(a, f, (__half *)buf);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmp

@@ -1,0 +1,58 @@
+// Host-side launchers of the lbmp kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lattice.cuh"
+
+namespace lbmp {
+
+// Number of FP64 quantities a reduction block writes:
+// sum u_x, sum u_y, sum (rho - rho0), sum |u|^2, sum |u - u_prev|^2,
+// count of non-finite nodes.
+constexpr int kNQ = 6;
+
+struct MacroOut {
+  double *rho;       // [ny][nx] or NULL
+  double *ux;        // [ny][nx] or NULL
+  double *uy;        // [ny][nx] or NULL
+  double *pops;      // [9][ny][nx] or NULL
+  float2 *uprev;     // [ny][pitch] velocity snapshot, or NULL
+  int update_prev;   // overwrite uprev with u after reading it
+  double *partials;  // [blocks][kNQ] or NULL (no reduction)
+};
+
+// Beskok-Karniadakis-Civan factor (Eq. 6-7, b = -1); f_c(0) = 1.
+__host__ __device__ inline double fc_bkc(double kn) {
+  if (kn == 0.0) return 1.0;
+  const double slip_b = -1.0;
+  const double alpha = 1.358 / (1.0 + 0.170 * pow(kn, -0.4348));
+  return (1.0 + alpha * kn) * (1.0 + 4.0 * kn / (1.0 - slip_b * kn));
+}
+
+// One time step over rows [a.y0, a.y0 + rows).
+cudaError_t launch_step(int storage, const StepArgs &a, int rows, const void *fin,
+                        void *fout, const float2 *med, cudaStream_t s);
+
+// Blocks a macroscopic/reduction launch over all ny rows uses.
+int macro_blocks(const StepArgs &a);
+cudaError_t launch_macro(int storage, const StepArgs &a, const void *fin,
+                         const float2 *med, const MacroOut &o, cudaStream_t s);
+
+// Sum [nblocks][nq] partials in a fixed order into out[0..nq).
+cudaError_t launch_finalize(const double *partials, int nblocks, int nq, double *out,
+                            cudaStream_t s);
+
+// Medium precompute: (eps, k_i, Kn) -> float2 (eps, 1/k_a); flags invalid
+// values in *bad; FP64 partial sums of eps over rows [y_lo, y_hi).
+int medium_blocks(int nx, int ny);
+cudaError_t launch_medium(const double *eps, const double *k_i, const double *kn,
+                          int nx, int ny, int pitch, int y_lo, int y_hi, float2 *med,
+                          unsigned *bad, double *partials, cudaStream_t s);
+
+// Inverse of the pull: write a post-collision buffer whose pull gives the
+// post-stream populations f ([9][ny][nx] float64).
+cudaError_t launch_load_pops(int storage, const StepArgs &a, int rows, const double *f,
+                             void *buf, cudaStream_t s);
+
+}  // namespace lbmp

@@ -1,0 +1,692 @@
+// C ABI of the GB300 porous lattice Boltzmann library (declared in lbmp.h).
+//
+// Host-side logic only: parameter validation, device buffers, launches,
+// CUDA graphs for the step loop, reductions read back in FP64, checkpoints.
+// Every compute step runs in the kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbmp.h"
+#include "kernels.h"
+
+using lbmp::StepArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbmp_status fail(lbmp_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+lbmp_status cuda_fail(cudaError_t e, const char *what) {
+  cudaGetLastError();  // clear a sticky-free error so later calls can proceed
+  if (e == cudaErrorMemoryAllocation)
+    return fail(LBMP_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(LBMP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBMP_CK(call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);      \
+  } while (0)
+
+constexpr int kPitchAlign = 64;   // elements: 256 B rows for FP32, 128 B for FP16
+constexpr int kGraphSteps = 32;   // even, so a replay keeps the buffer parity
+constexpr uint64_t kStateMagic = 0x4c424d5053544131ull;  // "LBMPSTA1"
+
+struct StateHeader {
+  uint64_t magic;
+  int32_t nx, ny, pitch, storage;
+  int64_t steps;
+  int32_t cur, pad;
+  double scale;
+  uint64_t payload_bytes;
+};
+
+}  // namespace
+
+struct lbmp_ctx {
+  lbmp_params p{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  int pitch = 0;
+  long long plane = 0;
+  int y_lo = 0, y_hi = 0;   // fluid rows [y_lo, y_hi)
+  size_t elem = 4;
+  void *buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  float2 *med = nullptr;
+  float2 *uprev = nullptr;
+  double *partials = nullptr;
+  int partials_blocks = 0;
+  double *results = nullptr;    // device, kNQ doubles
+  double *h_results = nullptr;  // pinned host, kNQ doubles
+  unsigned *d_flag = nullptr;
+  bool fields_set = false;
+  int64_t steps = 0;
+  int64_t launches = 0;
+  double scale = 1.0;
+  double eps_mean = 1.0;
+  int64_t fluid_nodes = 0;
+  int64_t device_bytes = 0;
+  int alloc_count = 0;
+  int fault_alloc_at = 0;       // simulated allocation failure (testing)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+  StepArgs args() const {
+    StepArgs a;
+    a.nx = p.nx;
+    a.ny = p.ny;
+    a.pitch = pitch;
+    a.y0 = y_lo;
+    a.plane = plane;
+    a.rho0 = (float)p.rho0;
+    a.drho_in = (float)(p.rho_in - p.rho0);
+    a.drho_out = (float)(p.rho_out - p.rho0);
+    a.omega = (float)(1.0 / p.tau);
+    a.cforce = (float)(1.0 - 0.5 / p.tau);
+    a.nu = (float)((p.tau - 0.5) / 3.0 / p.J);
+    a.Gx = (float)p.Gx;
+    a.Gy = (float)p.Gy;
+    a.fe_half = (float)(0.5 * 1.75 / std::sqrt(150.0));
+    a.scale = (float)scale;
+    a.inv_scale = (float)(1.0 / scale);
+    a.walls = p.bc_y == LBMP_BCY_WALLS;
+    a.pressure = p.bc_x == LBMP_BCX_PRESSURE;
+    a.forch = p.forchheimer != 0;
+    return a;
+  }
+  int rows() const { return y_hi - y_lo; }
+  size_t buf_bytes() const { return (size_t)plane * 9 * elem; }
+};
+
+namespace {
+
+lbmp_status dalloc(lbmp_ctx *c, void **ptr, size_t bytes, const char *what) {
+  *ptr = nullptr;
+  c->alloc_count++;
+  if (c->fault_alloc_at > 0 && c->alloc_count == c->fault_alloc_at)
+    return fail(LBMP_ENOMEM, "%s: simulated allocation failure (LBMP_FAULT_ALLOC)", what);
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return cuda_fail(e, what);
+  }
+  c->device_bytes += (int64_t)bytes;
+  return LBMP_OK;
+}
+
+void free_graphs(lbmp_ctx *c) {
+  for (auto &g : c->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+void release(lbmp_ctx *c) {
+  if (!c) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_graphs(c);
+  cudaFree(c->buf[0]);
+  cudaFree(c->buf[1]);
+  cudaFree(c->med);
+  cudaFree(c->uprev);
+  cudaFree(c->partials);
+  cudaFree(c->results);
+  cudaFree(c->d_flag);
+  if (c->h_results) cudaFreeHost(c->h_results);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete c;
+}
+
+lbmp_status set_device(lbmp_ctx *c) {
+  LBMP_CK(cudaSetDevice(c->device));
+  return LBMP_OK;
+}
+
+// Device scratch for caller pointers that live on the host.
+struct DevTemp {
+  void *ptr = nullptr;
+  ~DevTemp() {
+    if (ptr) cudaFree(ptr);
+  }
+};
+
+// Run the macroscopic/reduction kernel and, when partials are requested,
+// reduce them into c->h_results (synchronous).
+lbmp_status run_macro(lbmp_ctx *c, lbmp::MacroOut o, bool reduce) {
+  StepArgs a = c->args();
+  a.y0 = 0;
+  if (reduce) o.partials = c->partials;
+  LBMP_CK(lbmp::launch_macro(c->p.storage, a, c->buf[c->cur], c->med, o, c->stream));
+  c->launches++;
+  if (reduce) {
+    LBMP_CK(lbmp::launch_finalize(c->partials, lbmp::macro_blocks(a), lbmp::kNQ,
+                                  c->results, c->stream));
+    c->launches++;
+    LBMP_CK(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * lbmp::kNQ,
+                            cudaMemcpyDeviceToHost, c->stream));
+  }
+  LBMP_CK(cudaStreamSynchronize(c->stream));
+  if (reduce && c->h_results[5] != 0.0)
+    return fail(LBMP_ENAN, "%.0f fluid nodes have a non-finite density or velocity",
+                c->h_results[5]);
+  return LBMP_OK;
+}
+
+lbmp_status launch_steps(lbmp_ctx *c, int64_t n) {
+  StepArgs a = c->args();
+  for (int64_t t = 0; t < n; ++t) {
+    LBMP_CK(lbmp::launch_step(c->p.storage, a, c->rows(), c->buf[c->cur],
+                              c->buf[c->cur ^ 1], c->med, c->stream));
+    c->cur ^= 1;
+    c->launches++;
+  }
+  return LBMP_OK;
+}
+
+// Graph of kGraphSteps steps starting from buffer `cur` (captured once per
+// medium: the launch arguments hold the storage scale).
+lbmp_status get_graph(lbmp_ctx *c, int cur, cudaGraphExec_t *out) {
+  if (c->graph[cur]) {
+    *out = c->graph[cur];
+    return LBMP_OK;
+  }
+  StepArgs a = c->args();
+  cudaGraph_t g = nullptr;
+  LBMP_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int b = cur;
+  cudaError_t err = cudaSuccess;
+  for (int t = 0; t < kGraphSteps && err == cudaSuccess; ++t) {
+    err = lbmp::launch_step(c->p.storage, a, c->rows(), c->buf[b], c->buf[b ^ 1], c->med,
+                            c->cap_stream);
+    b ^= 1;
+  }
+  cudaError_t end = cudaStreamEndCapture(c->cap_stream, &g);
+  if (err != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(err, "graph capture of the step loop");
+  }
+  if (end != cudaSuccess) return cuda_fail(end, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+  c->graph[cur] = exec;
+  *out = exec;
+  return LBMP_OK;
+}
+
+bool valid_where(int32_t w) { return w == LBMP_HOST || w == LBMP_DEVICE; }
+
+}  // namespace
+
+extern "C" {
+
+const char *lbmp_last_error(void) { return g_err.c_str(); }
+
+double lbmp_fc(double kn) {
+  if (!(kn >= 0.0)) return NAN;
+  return lbmp::fc_bkc(kn);
+}
+
+lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
+  try {
+    if (!pin || !out) return fail(LBMP_EINVAL, "lbmp_create: NULL argument");
+    *out = nullptr;
+    lbmp_params p = *pin;
+    if (p.J == 0.0) p.J = 1.0;
+    if (p.rho0 == 0.0) p.rho0 = 1.0;
+    if (p.nx < 1 || p.ny < 1) return fail(LBMP_EINVAL, "nx, ny must be >= 1 (got %d x %d)", p.nx, p.ny);
+    if (p.nx > (1 << 30)) return fail(LBMP_EINVAL, "nx must be <= 2^30");
+    if (p.ny > 65535) return fail(LBMP_EINVAL, "ny must be <= 65535");
+    if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return fail(LBMP_EINVAL, "tau must be > 0.5 (got %g)", p.tau);
+    if (!(p.J > 0.0) || !std::isfinite(p.J)) return fail(LBMP_EINVAL, "J must be > 0");
+    if (!std::isfinite(p.Gx) || !std::isfinite(p.Gy)) return fail(LBMP_EINVAL, "G must be finite");
+    if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0)) return fail(LBMP_EINVAL, "rho0 must be > 0");
+    if (p.bc_x != LBMP_BCX_PERIODIC && p.bc_x != LBMP_BCX_PRESSURE)
+      return fail(LBMP_EINVAL, "bc_x must be LBMP_BCX_PERIODIC or LBMP_BCX_PRESSURE");
+    if (p.bc_y != LBMP_BCY_PERIODIC && p.bc_y != LBMP_BCY_WALLS)
+      return fail(LBMP_EINVAL, "bc_y must be LBMP_BCY_PERIODIC or LBMP_BCY_WALLS");
+    if (p.bc_x == LBMP_BCX_PRESSURE) {
+      if (p.nx < 3) return fail(LBMP_EINVAL, "pressure columns need nx >= 3");
+      if (!(p.rho_in > 0.0) || !(p.rho_out > 0.0) || !std::isfinite(p.rho_in) ||
+          !std::isfinite(p.rho_out))
+        return fail(LBMP_EINVAL, "rho_in and rho_out must be finite and > 0");
+    }
+    if (p.bc_y == LBMP_BCY_WALLS && p.ny < 3) return fail(LBMP_EINVAL, "walls need ny >= 3");
+    if (p.forchheimer != 0 && p.forchheimer != 1) return fail(LBMP_EINVAL, "forchheimer must be 0 or 1");
+    if (p.storage != LBMP_STORE_FP32 && p.storage != LBMP_STORE_FP16)
+      return fail(LBMP_EINVAL, "storage must be LBMP_STORE_FP32 or LBMP_STORE_FP16");
+    if (p.fp16_log2_scale < -60 || p.fp16_log2_scale > 60)
+      return fail(LBMP_EINVAL, "fp16_log2_scale must be in [-60, 60]");
+    if (p.reserved != 0) return fail(LBMP_EINVAL, "reserved must be 0");
+
+    lbmp_ctx *c = new (std::nothrow) lbmp_ctx();
+    if (!c) return fail(LBMP_ENOMEM, "host allocation of the context");
+    c->p = p;
+    if (const char *f = std::getenv("LBMP_FAULT_ALLOC")) c->fault_alloc_at = std::atoi(f);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "cudaGetDevice");
+    }
+    c->elem = (p.storage == LBMP_STORE_FP32) ? 4 : 2;
+    c->pitch = ((p.nx + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+    c->plane = (long long)c->pitch * p.ny;
+    c->y_lo = (p.bc_y == LBMP_BCY_WALLS) ? 1 : 0;
+    c->y_hi = (p.bc_y == LBMP_BCY_WALLS) ? p.ny - 1 : p.ny;
+    c->fluid_nodes = (int64_t)p.nx * (c->y_hi - c->y_lo);
+    lbmp_status st = LBMP_OK;
+#define LBMP_TRY(x)     \
+  do {                  \
+    st = (x);           \
+    if (st != LBMP_OK) { \
+      release(c);       \
+      return st;        \
+    }                   \
+  } while (0)
+    if (p.stream) {
+      c->stream = (cudaStream_t)p.stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) LBMP_TRY(cuda_fail(e, "cudaStreamCreate"));
+      c->own_stream = true;
+    }
+    e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) LBMP_TRY(cuda_fail(e, "cudaStreamCreate (capture)"));
+    StepArgs a = c->args();
+    a.y0 = 0;
+    c->partials_blocks = std::max(lbmp::macro_blocks(a), lbmp::medium_blocks(p.nx, p.ny));
+    LBMP_TRY(dalloc(c, &c->buf[0], c->buf_bytes(), "population buffer A"));
+    LBMP_TRY(dalloc(c, &c->buf[1], c->buf_bytes(), "population buffer B"));
+    LBMP_TRY(dalloc(c, (void **)&c->med, (size_t)c->plane * sizeof(float2), "medium"));
+    LBMP_TRY(dalloc(c, (void **)&c->uprev, (size_t)c->plane * sizeof(float2), "velocity snapshot"));
+    LBMP_TRY(dalloc(c, (void **)&c->partials,
+                    (size_t)c->partials_blocks * lbmp::kNQ * sizeof(double), "reduction partials"));
+    LBMP_TRY(dalloc(c, (void **)&c->results, lbmp::kNQ * sizeof(double), "reduction results"));
+    LBMP_TRY(dalloc(c, (void **)&c->d_flag, sizeof(unsigned), "validation flag"));
+    e = cudaMallocHost((void **)&c->h_results, lbmp::kNQ * sizeof(double));
+    if (e != cudaSuccess) LBMP_TRY(cuda_fail(e, "cudaMallocHost"));
+#undef LBMP_TRY
+    *out = c;
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_create: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_destroy(lbmp_ctx *c) {
+  try {
+    release(c);
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_destroy: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
+                            const double *kn, int32_t where) {
+  try {
+    if (!c || !eps || !k_i || !kn) return fail(LBMP_EINVAL, "lbmp_set_fields: NULL argument");
+    if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    const lbmp_params &p = c->p;
+    const size_t n = (size_t)p.nx * p.ny;
+    const double *de = eps, *dk = k_i, *dn = kn;
+    DevTemp tmp;
+    if (where == LBMP_HOST) {
+      cudaError_t e = cudaMalloc(&tmp.ptr, 3 * n * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e, "staging buffer for the medium");
+      double *t = (double *)tmp.ptr;
+      LBMP_CK(cudaMemcpyAsync(t, eps, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      LBMP_CK(cudaMemcpyAsync(t + n, k_i, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      LBMP_CK(cudaMemcpyAsync(t + 2 * n, kn, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      de = t;
+      dk = t + n;
+      dn = t + 2 * n;
+    }
+    LBMP_CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
+    LBMP_CK(lbmp::launch_medium(de, dk, dn, p.nx, p.ny, c->pitch, c->y_lo, c->y_hi, c->med,
+                                c->d_flag, c->partials, c->stream));
+    c->launches++;
+    LBMP_CK(lbmp::launch_finalize(c->partials, lbmp::medium_blocks(p.nx, p.ny), lbmp::kNQ,
+                                  c->results, c->stream));
+    c->launches++;
+    unsigned flag = 0;
+    LBMP_CK(cudaMemcpyAsync(c->h_results, c->results, lbmp::kNQ * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
+    LBMP_CK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                            c->stream));
+    LBMP_CK(cudaStreamSynchronize(c->stream));
+    if (flag) {
+      c->fields_set = false;
+      return fail(LBMP_EINVAL,
+                  "lbmp_set_fields: invalid values (%s%s%s%s); the context needs new fields",
+                  (flag & 1u) ? "eps outside [0,1] " : "", (flag & 2u) ? "k_i not > 0 " : "",
+                  (flag & 4u) ? "Kn negative or not finite " : "",
+                  (flag & 8u) ? "k_a below 1e-15" : "");
+    }
+    c->eps_mean = c->h_results[0] / c->h_results[1];
+    // storage scale S = 2^s for FP16: keep the expected largest deviation
+    // near 2^10, far from both the FP16 overflow and its subnormal range.
+    if (p.storage == LBMP_STORE_FP16) {
+      int s = p.fp16_log2_scale;
+      if (s == 0) {
+        double dev = 0.0;
+        if (p.bc_x == LBMP_BCX_PRESSURE)
+          dev = std::max(std::fabs(p.rho_in - p.rho0), std::fabs(p.rho_out - p.rho0));
+        const double L = (p.bc_y == LBMP_BCY_WALLS) ? (double)(p.ny - 2) : (double)std::max(p.nx, p.ny);
+        const double nu = (p.tau - 0.5) / 3.0 / p.J;
+        const double g = std::sqrt(p.Gx * p.Gx + p.Gy * p.Gy);
+        dev = std::max(dev, 3.0 * p.rho0 * g * L * L / (8.0 * nu));
+        dev = std::max(dev, 1e-7);
+        s = (int)std::floor(std::log2(1024.0 / dev));
+        s = std::min(60, std::max(-60, s));
+      }
+      c->scale = std::ldexp(1.0, s);
+    } else {
+      c->scale = 1.0;
+    }
+    free_graphs(c);
+    LBMP_CK(cudaMemsetAsync(c->buf[0], 0, c->buf_bytes(), c->stream));
+    LBMP_CK(cudaMemsetAsync(c->buf[1], 0, c->buf_bytes(), c->stream));
+    LBMP_CK(cudaMemsetAsync(c->uprev, 0, (size_t)c->plane * sizeof(float2), c->stream));
+    LBMP_CK(cudaStreamSynchronize(c->stream));
+    c->cur = 0;
+    c->steps = 0;
+    c->fields_set = true;
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_set_fields: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_step(lbmp_ctx *c, int64_t n) {
+  try {
+    if (!c) return fail(LBMP_EINVAL, "lbmp_step: NULL context");
+    if (n < 0) return fail(LBMP_EINVAL, "lbmp_step: n must be >= 0");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_step: call lbmp_set_fields first");
+    if (n == 0) return LBMP_OK;
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    int64_t left = n;
+    while (left >= kGraphSteps) {
+      cudaGraphExec_t g = nullptr;
+      st = get_graph(c, c->cur, &g);
+      if (st) return st;
+      LBMP_CK(cudaGraphLaunch(g, c->stream));
+      c->launches += kGraphSteps;
+      left -= kGraphSteps;
+    }
+    st = launch_steps(c, left);
+    if (st) return st;
+    c->steps += n;
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_step: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_synchronize(lbmp_ctx *c) {
+  if (!c) return fail(LBMP_EINVAL, "lbmp_synchronize: NULL context");
+  lbmp_status st = set_device(c);
+  if (st) return st;
+  LBMP_CK(cudaStreamSynchronize(c->stream));
+  return LBMP_OK;
+}
+
+lbmp_status lbmp_macroscopic(lbmp_ctx *c, double *rho, double *ux, double *uy,
+                             int32_t where) {
+  try {
+    if (!c) return fail(LBMP_EINVAL, "lbmp_macroscopic: NULL context");
+    if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_macroscopic: no fields set");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    lbmp::MacroOut o{};
+    DevTemp tmp;
+    if (where == LBMP_HOST) {
+      cudaError_t e = cudaMalloc(&tmp.ptr, 3 * n * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+      double *t = (double *)tmp.ptr;
+      o.rho = rho ? t : nullptr;
+      o.ux = ux ? t + n : nullptr;
+      o.uy = uy ? t + 2 * n : nullptr;
+    } else {
+      o.rho = rho;
+      o.ux = ux;
+      o.uy = uy;
+    }
+    st = run_macro(c, o, false);
+    if (st) return st;
+    if (where == LBMP_HOST) {
+      double *t = (double *)tmp.ptr;
+      if (rho) LBMP_CK(cudaMemcpy(rho, t, n * sizeof(double), cudaMemcpyDeviceToHost));
+      if (ux) LBMP_CK(cudaMemcpy(ux, t + n, n * sizeof(double), cudaMemcpyDeviceToHost));
+      if (uy) LBMP_CK(cudaMemcpy(uy, t + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_macroscopic: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_populations(lbmp_ctx *c, double *f, int32_t where) {
+  try {
+    if (!c || !f) return fail(LBMP_EINVAL, "lbmp_populations: NULL argument");
+    if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_populations: no fields set");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    const size_t n = (size_t)c->p.nx * c->p.ny * 9;
+    lbmp::MacroOut o{};
+    DevTemp tmp;
+    if (where == LBMP_HOST) {
+      cudaError_t e = cudaMalloc(&tmp.ptr, n * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+      o.pops = (double *)tmp.ptr;
+    } else {
+      o.pops = f;
+    }
+    st = run_macro(c, o, false);
+    if (st) return st;
+    if (where == LBMP_HOST)
+      LBMP_CK(cudaMemcpy(f, tmp.ptr, n * sizeof(double), cudaMemcpyDeviceToHost));
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_populations: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_set_populations(lbmp_ctx *c, const double *f, int32_t where) {
+  try {
+    if (!c || !f) return fail(LBMP_EINVAL, "lbmp_set_populations: NULL argument");
+    if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_set_populations: no fields set");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    const size_t n = (size_t)c->p.nx * c->p.ny * 9;
+    const double *src = f;
+    DevTemp tmp;
+    if (where == LBMP_HOST) {
+      cudaError_t e = cudaMalloc(&tmp.ptr, n * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+      LBMP_CK(cudaMemcpyAsync(tmp.ptr, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      src = (const double *)tmp.ptr;
+    }
+    StepArgs a = c->args();
+    LBMP_CK(lbmp::launch_load_pops(c->p.storage, a, c->rows(), src, c->buf[c->cur], c->stream));
+    c->launches++;
+    LBMP_CK(cudaStreamSynchronize(c->stream));
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_set_populations: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_permeability(lbmp_ctx *c, double *k_g, double *u_mean) {
+  try {
+    if (!c) return fail(LBMP_EINVAL, "lbmp_permeability: NULL context");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_permeability: no fields set");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    lbmp::MacroOut o{};
+    st = run_macro(c, o, true);
+    if (st) return st;
+    const lbmp_params &p = c->p;
+    const double um = c->h_results[0] / (double)c->fluid_nodes;
+    double g = p.Gx;
+    if (p.bc_x == LBMP_BCX_PRESSURE)
+      g += (p.rho_in - p.rho_out) / 3.0 / c->eps_mean / (p.rho0 * (double)(p.nx - 1));
+    const double nu = (p.tau - 0.5) / 3.0 / p.J;
+    if (u_mean) *u_mean = um;
+    if (k_g) *k_g = nu * um / g;
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_permeability: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_residual(lbmp_ctx *c, double *r) {
+  try {
+    if (!c || !r) return fail(LBMP_EINVAL, "lbmp_residual: NULL argument");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_residual: no fields set");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    lbmp::MacroOut o{};
+    o.uprev = c->uprev;
+    o.update_prev = 1;
+    st = run_macro(c, o, true);
+    if (st) return st;
+    *r = std::sqrt(c->h_results[4]) / std::sqrt(c->h_results[3]);
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_residual: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_mass(lbmp_ctx *c, double *m) {
+  try {
+    if (!c || !m) return fail(LBMP_EINVAL, "lbmp_mass: NULL argument");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_mass: no fields set");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    lbmp::MacroOut o{};
+    st = run_macro(c, o, true);
+    if (st) return st;
+    *m = (double)c->fluid_nodes * c->p.rho0 + c->h_results[2];
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_mass: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_state_size(lbmp_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return fail(LBMP_EINVAL, "lbmp_state_size: NULL argument");
+  *bytes = sizeof(StateHeader) + c->buf_bytes();
+  return LBMP_OK;
+}
+
+lbmp_status lbmp_get_state(lbmp_ctx *c, void *buf, size_t bytes, int32_t where) {
+  try {
+    if (!c || !buf) return fail(LBMP_EINVAL, "lbmp_get_state: NULL argument");
+    if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_get_state: no fields set");
+    size_t need = sizeof(StateHeader) + c->buf_bytes();
+    if (bytes < need) return fail(LBMP_EINVAL, "lbmp_get_state: buffer of %zu bytes, need %zu", bytes, need);
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.nx = c->p.nx;
+    h.ny = c->p.ny;
+    h.pitch = c->pitch;
+    h.storage = c->p.storage;
+    h.steps = c->steps;
+    h.cur = 0;
+    h.scale = c->scale;
+    h.payload_bytes = c->buf_bytes();
+    cudaMemcpyKind k = (where == LBMP_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaMemcpyKind kh = (where == LBMP_HOST) ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
+    LBMP_CK(cudaStreamSynchronize(c->stream));
+    LBMP_CK(cudaMemcpy(buf, &h, sizeof(h), kh));
+    LBMP_CK(cudaMemcpy((char *)buf + sizeof(h), c->buf[c->cur], c->buf_bytes(), k));
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_get_state: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_set_state(lbmp_ctx *c, const void *buf, size_t bytes, int32_t where) {
+  try {
+    if (!c || !buf) return fail(LBMP_EINVAL, "lbmp_set_state: NULL argument");
+    if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_set_state: set the medium first");
+    size_t need = sizeof(StateHeader) + c->buf_bytes();
+    if (bytes != need) return fail(LBMP_EINVAL, "lbmp_set_state: %zu bytes, expected %zu", bytes, need);
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    StateHeader h{};
+    cudaMemcpyKind kh = (where == LBMP_HOST) ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+    LBMP_CK(cudaMemcpy(&h, buf, sizeof(h), kh));
+    if (h.magic != kStateMagic || h.nx != c->p.nx || h.ny != c->p.ny || h.pitch != c->pitch ||
+        h.storage != c->p.storage || h.payload_bytes != c->buf_bytes())
+      return fail(LBMP_EINVAL, "lbmp_set_state: blob does not match this context");
+    if (h.scale != c->scale)
+      return fail(LBMP_EINVAL, "lbmp_set_state: blob written with FP16 scale %g, context uses %g",
+                  h.scale, c->scale);
+    cudaMemcpyKind k = (where == LBMP_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    LBMP_CK(cudaStreamSynchronize(c->stream));
+    LBMP_CK(cudaMemcpy(c->buf[c->cur], (const char *)buf + sizeof(h), c->buf_bytes(), k));
+    c->steps = h.steps;
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_set_state: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_get_info(lbmp_ctx *c, lbmp_info *out) {
+  if (!c || !out) return fail(LBMP_EINVAL, "lbmp_get_info: NULL argument");
+  out->nx = c->p.nx;
+  out->ny = c->p.ny;
+  out->pitch = c->pitch;
+  out->storage = c->p.storage;
+  out->fluid_nodes = c->fluid_nodes;
+  out->steps = c->steps;
+  // nine populations read and written once, plus the float2 medium
+  out->bytes_per_update = 2.0 * 9.0 * (double)c->elem + 8.0;
+  out->fp16_scale = c->scale;
+  out->eps_mean = c->eps_mean;
+  out->device_bytes = c->device_bytes;
+  out->launches = c->launches;
+  return LBMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,301 @@
+"""Python binding of the C ABI in ``include/lbmp.h`` (argument marshalling only).
+
+Every step of the lattice Boltzmann path runs in the CUDA kernels of
+``liblbmp.so``; this module converts torch tensors or numpy arrays to
+pointers and status codes to exceptions.  PyTorch supplies device memory and
+the CUDA stream.  There is no CPU fallback: if the library is not built, or
+no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbmp.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "lbmp.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENAN, ETIMEOUT = range(7)
+BCX_PERIODIC, BCX_PRESSURE = 0, 1
+BCY_PERIODIC, BCY_WALLS = 0, 1
+STORE_FP32, STORE_FP16 = 0, 1
+HOST, DEVICE = 0, 1
+
+_STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE",
+           ENAN: "ENAN", ETIMEOUT: "ETIMEOUT"}
+
+
+class LbmpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lbmp {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``lbmp_params``."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("tau", ctypes.c_double), ("J", ctypes.c_double),
+        ("Gx", ctypes.c_double), ("Gy", ctypes.c_double),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("rho0", ctypes.c_double), ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
+        ("forchheimer", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("fp16_log2_scale", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Info(ctypes.Structure):
+    """Mirror of ``lbmp_info``."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("pitch", ctypes.c_int32),
+        ("storage", ctypes.c_int32), ("fluid_nodes", ctypes.c_int64),
+        ("steps", ctypes.c_int64), ("bytes_per_update", ctypes.c_double),
+        ("fp16_scale", ctypes.c_double), ("eps_mean", ctypes.c_double),
+        ("device_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
+    ]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def header_functions() -> list[str]:
+    """Names of the functions ``include/lbmp.h`` declares."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(lbmp_\w+)\s*\(", text, re.M)))
+
+
+def load(path: str = LIB_PATH):
+    """Load ``liblbmp.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblbmp.so not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    st = ctypes.c_int32
+    L.lbmp_last_error.restype = ctypes.c_char_p
+    L.lbmp_last_error.argtypes = []
+    L.lbmp_fc.restype = ctypes.c_double
+    L.lbmp_fc.argtypes = [ctypes.c_double]
+    L.lbmp_create.restype = st
+    L.lbmp_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_VP)]
+    L.lbmp_destroy.restype = st
+    L.lbmp_destroy.argtypes = [_VP]
+    L.lbmp_set_fields.restype = st
+    L.lbmp_set_fields.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int32]
+    L.lbmp_step.restype = st
+    L.lbmp_step.argtypes = [_VP, ctypes.c_int64]
+    L.lbmp_synchronize.restype = st
+    L.lbmp_synchronize.argtypes = [_VP]
+    L.lbmp_macroscopic.restype = st
+    L.lbmp_macroscopic.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int32]
+    L.lbmp_populations.restype = st
+    L.lbmp_populations.argtypes = [_VP, _VP, ctypes.c_int32]
+    L.lbmp_set_populations.restype = st
+    L.lbmp_set_populations.argtypes = [_VP, _VP, ctypes.c_int32]
+    L.lbmp_permeability.restype = st
+    L.lbmp_permeability.argtypes = [_VP, _D, _D]
+    L.lbmp_residual.restype = st
+    L.lbmp_residual.argtypes = [_VP, _D]
+    L.lbmp_mass.restype = st
+    L.lbmp_mass.argtypes = [_VP, _D]
+    L.lbmp_state_size.restype = st
+    L.lbmp_state_size.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
+    L.lbmp_get_state.restype = st
+    L.lbmp_get_state.argtypes = [_VP, _VP, ctypes.c_size_t, ctypes.c_int32]
+    L.lbmp_set_state.restype = st
+    L.lbmp_set_state.argtypes = [_VP, _VP, ctypes.c_size_t, ctypes.c_int32]
+    L.lbmp_get_info.restype = st
+    L.lbmp_get_info.argtypes = [_VP, ctypes.POINTER(Info)]
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != OK:
+        raise LbmpError(status, load().lbmp_last_error().decode())
+
+
+def fc(kn: float) -> float:
+    """Eq. 6-7 correction factor, evaluated by the library (host code)."""
+    return float(load().lbmp_fc(float(kn)))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+@dataclass
+class SimConfig:
+    nx: int
+    ny: int
+    tau: float = 0.8
+    J: float = 1.0
+    G: tuple = (0.0, 0.0)
+    bc_x: int = BCX_PERIODIC
+    bc_y: int = BCY_PERIODIC
+    rho0: float = 1.0
+    rho_in: float = 1.0
+    rho_out: float = 1.0
+    forchheimer: int = 0
+    storage: int = STORE_FP32
+    fp16_log2_scale: int = 0
+
+    def to_params(self, stream: int | None) -> Params:
+        return Params(int(self.nx), int(self.ny), float(self.tau), float(self.J),
+                      float(self.G[0]), float(self.G[1]), int(self.bc_x), int(self.bc_y),
+                      float(self.rho0), float(self.rho_in), float(self.rho_out),
+                      int(self.forchheimer), int(self.storage), int(self.fp16_log2_scale), 0,
+                      stream)
+
+
+class Sim:
+    """One lattice (``lbmp_ctx``) on the current CUDA device.
+
+    ``stream``: a ``torch.cuda.Stream`` the library queues its work on
+    (default: a new stream owned by this object).
+    """
+
+    def __init__(self, cfg: SimConfig, stream=None):
+        torch = _torch()
+        L = load()
+        if not torch.cuda.is_available():
+            raise LbmpError(ECUDA, "no CUDA device available")
+        self.cfg = cfg
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._params = cfg.to_params(self.stream.cuda_stream)
+        h = _VP()
+        _check(L.lbmp_create(ctypes.byref(self._params), ctypes.byref(h)))
+        self._h = h
+        self.nx, self.ny = cfg.nx, cfg.ny
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbmp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- marshalling helpers
+    def _in_field(self, a, shape):
+        """(pointer, where, keepalive) for a float64 input of ``shape``."""
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            t = a.detach()
+            if t.dtype != torch.float64:
+                t = t.to(torch.float64)
+            t = t.contiguous()
+            if tuple(t.shape) != tuple(shape):
+                t = t.expand(*shape).contiguous()
+            where = DEVICE if t.is_cuda else HOST
+            return ctypes.c_void_p(t.data_ptr()), where, t
+        arr = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
+        return arr.ctypes.data_as(ctypes.c_void_p), HOST, arr
+
+    def _out_field(self, shape, device: bool):
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device else "cpu"
+        t = torch.empty(shape, dtype=torch.float64, device=dev)
+        return t, ctypes.c_void_p(t.data_ptr()), (DEVICE if device else HOST)
+
+    # -- C ABI calls
+    def set_fields(self, eps, k_i, kn):
+        shape = (self.ny, self.nx)
+        pe, we, ke = self._in_field(eps, shape)
+        pk, wk, kk = self._in_field(k_i, shape)
+        pn, wn, kkn = self._in_field(kn, shape)
+        if not (we == wk == wn):
+            raise ValueError("eps, k_i and kn must all be on the host or all on the device")
+        if we == DEVICE:
+            _torch().cuda.current_stream().synchronize()
+        _check(load().lbmp_set_fields(self._h, pe, pk, pn, we))
+
+    def step(self, n: int = 1):
+        _check(load().lbmp_step(self._h, int(n)))
+
+    def synchronize(self):
+        _check(load().lbmp_synchronize(self._h))
+
+    def macroscopic(self, device: bool = True):
+        shape = (self.ny, self.nx)
+        rho, pr, w = self._out_field(shape, device)
+        ux, pu, _ = self._out_field(shape, device)
+        uy, pv, _ = self._out_field(shape, device)
+        _check(load().lbmp_macroscopic(self._h, pr, pu, pv, w))
+        return rho, ux, uy
+
+    def populations(self, device: bool = True):
+        f, pf, w = self._out_field((9, self.ny, self.nx), device)
+        _check(load().lbmp_populations(self._h, pf, w))
+        return f
+
+    def set_populations(self, f):
+        pf, w, keep = self._in_field(f, (9, self.ny, self.nx))
+        if w == DEVICE:
+            _torch().cuda.current_stream().synchronize()
+        _check(load().lbmp_set_populations(self._h, pf, w))
+
+    def permeability(self):
+        kg, um = ctypes.c_double(), ctypes.c_double()
+        _check(load().lbmp_permeability(self._h, ctypes.byref(kg), ctypes.byref(um)))
+        return kg.value, um.value
+
+    def residual(self) -> float:
+        r = ctypes.c_double()
+        _check(load().lbmp_residual(self._h, ctypes.byref(r)))
+        return r.value
+
+    def mass(self) -> float:
+        m = ctypes.c_double()
+        _check(load().lbmp_mass(self._h, ctypes.byref(m)))
+        return m.value
+
+    def state_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(load().lbmp_state_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_state(self) -> np.ndarray:
+        buf = np.empty(self.state_size(), dtype=np.uint8)
+        _check(load().lbmp_get_state(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes, HOST))
+        return buf
+
+    def set_state(self, blob: np.ndarray):
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(load().lbmp_set_state(self._h, blob.ctypes.data_as(ctypes.c_void_p), blob.nbytes, HOST))
+
+    def info(self) -> Info:
+        out = Info()
+        _check(load().lbmp_get_info(self._h, ctypes.byref(out)))
+        return out
+
+    def run_to_steady(self, tol: float, check_every: int = 100, max_steps: int = 2_000_000):
+        """Step until the relative velocity residual over ``check_every``
+        steps is below ``tol`` (FP32 storage floors near 1e-7)."""
+        self.residual()
+        while self.info().steps < max_steps:
+            self.step(check_every)
+            r = self.residual()
+            if r < tol:
+                return r
+        raise RuntimeError(f"residual did not reach {tol} in {max_steps} steps")

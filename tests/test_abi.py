@@ -1,0 +1,69 @@
+"""C ABI: the library loads, exports every function the header declares,
+and validates parameters before touching a GPU (no GPU needed)."""
+import ctypes
+import math
+
+import pytest
+
+from paper_1411_7051_gb300 import build, lbmp
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return lbmp.load()
+
+
+def test_exports_every_declared_function(L):
+    names = lbmp.header_functions()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/lbmp.h but not exported"
+
+
+def test_fc_host_function(L, orc):
+    # library's host f_c against the oracle's (Eq. 6-7)
+    for kn in (0.0, 1e-6, 1e-3, 0.1, 0.339, 1.0, 9.16, 10.0, 1e4):
+        assert lbmp.fc(kn) == pytest.approx(orc.fc(kn), rel=1e-15, abs=0)
+    assert math.isnan(lbmp.fc(-1.0))
+    assert math.isnan(lbmp.fc(float("nan")))
+
+
+def _create(L, **kw):
+    cfg = lbmp.SimConfig(**{"nx": 8, "ny": 8, **kw})
+    p = cfg.to_params(None)
+    h = ctypes.c_void_p()
+    st = L.lbmp_create(ctypes.byref(p), ctypes.byref(h))
+    if st == lbmp.OK:
+        L.lbmp_destroy(h)
+    return st, L.lbmp_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,needle", [
+    ({"nx": 0}, "nx, ny"),
+    ({"ny": -3}, "nx, ny"),
+    ({"ny": 70000}, "ny must be"),
+    ({"tau": 0.5}, "tau"),
+    ({"tau": float("nan")}, "tau"),
+    ({"J": -1.0}, "J"),
+    ({"G": (float("inf"), 0.0)}, "G must"),
+    ({"bc_x": 7}, "bc_x"),
+    ({"bc_y": 2}, "bc_y"),
+    ({"bc_x": lbmp.BCX_PRESSURE, "nx": 2}, "nx >= 3"),
+    ({"bc_x": lbmp.BCX_PRESSURE, "rho_in": 0.0}, "rho_in"),
+    ({"bc_y": lbmp.BCY_WALLS, "ny": 2}, "ny >= 3"),
+    ({"forchheimer": 2}, "forchheimer"),
+    ({"storage": 5}, "storage"),
+    ({"fp16_log2_scale": 100}, "fp16_log2_scale"),
+])
+def test_create_rejects_bad_parameters(L, kw, needle):
+    st, msg = _create(L, **kw)
+    assert st == lbmp.EINVAL, (st, msg)
+    assert needle in msg
+
+
+def test_null_arguments(L):
+    assert L.lbmp_create(None, None) == lbmp.EINVAL
+    assert L.lbmp_destroy(None) == lbmp.OK
+    assert L.lbmp_step(None, 1) == lbmp.EINVAL
+    assert L.lbmp_get_info(None, None) == lbmp.EINVAL
