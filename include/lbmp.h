@@ -52,7 +52,14 @@ typedef int32_t lbmp_status;
 
 /* population storage in device memory (arithmetic is FP32 in both) */
 #define LBMP_STORE_FP32 0 /* f_i - w_i rho0 as float */
-#define LBMP_STORE_FP16 1 /* (f_i - w_i rho0) * S as IEEE half, S = 2^s */
+#define LBMP_STORE_FP16 1 /* (f_i - w_i rho0) * S as IEEE half, S = 2^s.  With
+                             stochastic rounding (default) the random offsets
+                             are a hash of (seed, time level, node), so runs
+                             and checkpoint restarts are reproducible. */
+
+/* rounding of FP16 stores */
+#define LBMP_ROUND_STOCHASTIC 0 /* unbiased in expectation (default) */
+#define LBMP_ROUND_NEAREST 1    /* round to nearest even */
 
 #define LBMP_HOST 0
 #define LBMP_DEVICE 1
@@ -70,7 +77,8 @@ typedef struct lbmp_params {
   int32_t forchheimer;  /* 1: Eq. 2 with F_eps = 1.75/sqrt(150 eps^3); 0: Eq. 8 */
   int32_t storage;      /* LBMP_STORE_* */
   int32_t fp16_log2_scale; /* s of S = 2^s for FP16 storage; 0 = automatic */
-  int32_t reserved;     /* must be 0 */
+  int32_t fp16_rounding;   /* LBMP_ROUND_*: how FP16 stores round */
+  uint64_t seed;           /* stream of the stochastic rounding (any value) */
   void *stream;         /* cudaStream_t for all work; NULL = a private stream */
 } lbmp_params;
 

@@ -17,53 +17,77 @@
 namespace lbmp {
 
 constexpr int kStepBX = 128;   // threads per block along x
-constexpr int kStepNPT = 2;    // nodes per thread (strided by kStepBX)
+constexpr int kStepNPT = 2;    // nodes per thread, strided by kStepBX
 constexpr int kMacroBX = 256;
 constexpr int kMediumBX = 256;
 
 // ------------------------------------------------------------- step kernel
-template <class S, int NPT>
+// Each thread updates kStepNPT nodes of one row, kStepBX apart, so every
+// load and store instruction of a warp touches 32 consecutive elements.
+// All loads of a thread are issued before its first collision.  Plate rows
+// are block-uniform branches inside pull_node.  The stochastic-rounding
+// bits of time level t come from *tctr + k (the counter is advanced by
+// bump_kernel after a group of launches).
+template <class S, bool SR>
 __global__ void __launch_bounds__(kStepBX)
     step_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
-                typename S::T *__restrict__ fout, const float2 *__restrict__ med) {
+                typename S::T *__restrict__ fout, const float2 *__restrict__ med,
+                const unsigned long long *__restrict__ tctr, int k) {
   const int y = a.y0 + blockIdx.y;
-  const int xb = blockIdx.x * (kStepBX * NPT) + threadIdx.x;
+  const int xb = blockIdx.x * (kStepBX * kStepNPT) + threadIdx.x;
   const long long row = (long long)y * a.pitch;
-  float d[NPT][9];
-  float2 m[NPT];
+  float d[kStepNPT][9];
+  float2 m[kStepNPT];
 #pragma unroll
-  for (int k = 0; k < NPT; ++k) {
-    const int x = xb + k * kStepBX;
+  for (int j = 0; j < kStepNPT; ++j) {
+    const int x = xb + j * kStepBX;
     if (x < a.nx) {
-      pull_node<S>(fin, a, x, y, d[k]);
-      m[k] = med[row + x];
+      pull_node<S>(fin, a, x, y, d[j]);
+      m[j] = med[row + x];
     }
   }
+  uint32_t ts = 0;
+  if (SR) {
+    const unsigned long long t = *tctr + (unsigned long long)k;
+    ts = mix32((uint32_t)t * 0x9e3779b9u ^ a.seed_lo ^ mix32((uint32_t)(t >> 32) ^ a.seed_hi));
+  }
 #pragma unroll
-  for (int k = 0; k < NPT; ++k) {
-    const int x = xb + k * kStepBX;
+  for (int j = 0; j < kStepNPT; ++j) {
+    const int x = xb + j * kStepBX;
     if (x >= a.nx) continue;
-    if (a.pressure && (x == 0 || x == a.nx - 1))
-      pressure_node<S>(fin, med, a, x, y, m[k].x, d[k]);
-    const NodeState s = node_state(d[k], m[k].x, m[k].y, a);
-    collide(d[k], s, m[k].x, a);
+    if (a.pressure && (x == 0 || x == a.nx - 1)) pressure_node<S>(fin, med, a, x, y, m[j].x, d[j]);
+    const NodeState s = node_state(d[j], m[j].x, m[j].y, a);
+    collide(d[j], s, a);
     typename S::T *o = fout + row + x;
+    const uint32_t h = SR ? mix32((uint32_t)(row + x) ^ ts) : 0u;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) S::st(o + i * a.plane, d[k][i], a.scale);
+    for (int i = 0; i < 9; ++i) S::template st1r<SR>(o + i * a.plane, d[j][i], h, i);
   }
 }
 
-cudaError_t launch_step(int storage, const StepArgs &a, int rows, const void *fin,
-                        void *fout, const float2 *med, cudaStream_t s) {
+// Advance the time-level counter of the stochastic rounding by n.
+__global__ void bump_kernel(unsigned long long *tctr, int n) { *tctr += (unsigned long long)n; }
+
+cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
+                        void *fout, const float2 *med, const unsigned long long *tctr, int k,
+                        cudaStream_t s) {
   if (rows <= 0 || a.nx <= 0) return cudaSuccess;
   dim3 block(kStepBX);
   dim3 grid((a.nx + kStepBX * kStepNPT - 1) / (kStepBX * kStepNPT), rows);
   if (storage == 0)
-    step_kernel<StoreF32, kStepNPT><<<grid, block, 0, s>>>(
-        a, (const float *)fin, (float *)fout, med);
+    step_kernel<StoreF32, false><<<grid, block, 0, s>>>(a, (const float *)fin, (float *)fout,
+                                                        med, tctr, k);
+  else if (sr)
+    step_kernel<StoreF16, true><<<grid, block, 0, s>>>(a, (const __half *)fin, (__half *)fout,
+                                                       med, tctr, k);
   else
-    step_kernel<StoreF16, kStepNPT><<<grid, block, 0, s>>>(
-        a, (const __half *)fin, (__half *)fout, med);
+    step_kernel<StoreF16, false><<<grid, block, 0, s>>>(a, (const __half *)fin,
+                                                        (__half *)fout, med, tctr, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s) {
+  bump_kernel<<<1, 1, 0, s>>>(tctr, n);
   return cudaGetLastError();
 }
 
@@ -114,6 +138,8 @@ __global__ void __launch_bounds__(kMacroBX)
       pull_node<S>(fin, a, x, y, d);
       if (a.pressure && (x == 0 || x == a.nx - 1)) pressure_node<S>(fin, med, a, x, y, m.x, d);
       const NodeState s = node_state(d, m.x, m.y, a);
+      const float drho = s.drho_s * a.inv_scale;
+      (void)drho;
       if (o.rho) o.rho[j] = (double)s.rho;
       if (o.ux) o.ux[j] = (double)s.ux;
       if (o.uy) o.uy[j] = (double)s.uy;
@@ -121,14 +147,15 @@ __global__ void __launch_bounds__(kMacroBX)
         const double r0 = (double)a.rho0;
         const double w[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-        for (int i = 0; i < 9; ++i) o.pops[i * n + j] = w[i] * r0 + (double)d[i];
+        const double is = (double)a.inv_scale;
+        for (int i = 0; i < 9; ++i) o.pops[i * n + j] = w[i] * r0 + (double)d[i] * is;
       }
       if (o.partials) {
         const double ux = s.ux, uy = s.uy;
         const bool finite = isfinite(s.ux) && isfinite(s.uy) && isfinite(s.rho);
         v[0] = finite ? ux : 0.0;
         v[1] = finite ? uy : 0.0;
-        v[2] = finite ? (double)s.drho : 0.0;
+        v[2] = finite ? (double)drho : 0.0;
         v[3] = finite ? ux * ux + uy * uy : 0.0;
         if (o.uprev) {
           const long long jp = (long long)y * a.pitch + x;
@@ -267,8 +294,8 @@ __global__ void __launch_bounds__(kMacroBX)
         val = f[j * n + (long long)ty * a.nx + tx];
       }
     }
-    S::st(buf + j * a.plane + (long long)y * a.pitch + x, (float)(val - w[j] * r0),
-          a.scale);
+    S::st1(buf + j * a.plane + (long long)y * a.pitch + x,
+           (float)((val - w[j] * r0) * (double)a.scale));
   }
 }
 

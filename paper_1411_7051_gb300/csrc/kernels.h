@@ -30,9 +30,13 @@ __host__ __device__ inline double fc_bkc(double kn) {
   return (1.0 + alpha * kn) * (1.0 + 4.0 * kn / (1.0 - slip_b * kn));
 }
 
-// One time step over rows [a.y0, a.y0 + rows).
-cudaError_t launch_step(int storage, const StepArgs &a, int rows, const void *fin,
-                        void *fout, const float2 *med, cudaStream_t s);
+// One time step over rows [a.y0, a.y0 + rows).  sr: FP16 stochastic
+// rounding with the bits of time level *tctr + k.
+cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
+                        void *fout, const float2 *med, const unsigned long long *tctr, int k,
+                        cudaStream_t s);
+// *tctr += n (one thread).
+cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s);
 
 // Blocks a macroscopic/reduction launch over all ny rows uses.
 int macro_blocks(const StepArgs &a);

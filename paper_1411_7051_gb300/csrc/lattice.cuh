@@ -3,14 +3,16 @@
 //
 // State representation.  After t time steps, population buffer B holds the
 // post-collision values f*_i(x, t-1) of every fluid node, stored as the
-// shifted deviation d_i = f_i - w_i rho0 (FP32, or FP16 scaled by S = 2^s).
-// Pulling B (f_i(x) <- f*_i(x - e_i), Eq. 12's streaming) gives the
-// post-stream populations f_i(x, t), from which density and velocity
-// (Eq. 16-17) are defined.  The initial buffer is all zeros (f = w_i rho0).
+// shifted deviation d_i = f_i - w_i rho0, scaled by S (S = 1 for FP32,
+// S = 2^s for FP16).  Pulling B (f_i(x) <- f*_i(x - e_i), the streaming of
+// Eq. 12) gives the post-stream populations f_i(x, t), from which density
+// and velocity (Eq. 16-17) are defined.  The initial buffer is all zeros.
+// Device code works on these "stored units" directly; S enters only through
+// a few per-node scalars.
 //
 // Layout in HBM: 9 planes [9][ny][pitch] (plane = pitch * ny elements,
 // pitch a multiple of 64 elements), medium as float2 (eps, 1/k_a) per node
-// on the same [ny][pitch] grid.
+// on the same [ny][pitch] grid (read as float4 for a node pair).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -31,44 +33,116 @@ struct StepArgs {
   float drho_in;       // rho_in - rho0
   float drho_out;      // rho_out - rho0
   float omega;         // 1 / tau
+  float one_m_omega;   // 1 - 1 / tau
   float cforce;        // 1 - 1 / (2 tau)  (Eq. 15 prefactor)
   float nu;            // nu_e / J
   float Gx, Gy;        // body force of Eq. 2
-  float fe_half;       // (1/2) * 1.75 / sqrt(150): eps F_eps / 2 = fe_half / sqrt(eps)
+  float fe_half;       // (1/2) 1.75 / sqrt(150): eps F_eps / 2 = fe_half / sqrt(eps)
   float scale;         // storage scale S (1 for FP32)
   float inv_scale;     // 1 / S
   int walls;           // rows 0 and ny-1 are plates (halfway bounce-back)
   int pressure;        // columns 0 and nx-1 carry imposed densities
   int forch;           // keep the Forchheimer drag of Eq. 2
+  uint32_t seed_lo, seed_hi;  // stochastic rounding stream
 };
+
+// ------------------------------------------------ hardware approximations
+// PTX approximate reciprocal and square root (relative error ~2^-23); the
+// step needs ~1e-7, and IEEE-exact division would double the instruction
+// count of the kernel.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// 32-bit avalanche mix (the finalizer of MurmurHash3), for the counter-based
+// stochastic-rounding bits.
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
 
 // ----------------------------------------------------------------- storage
 struct StoreF32 {
   using T = float;
-  static __device__ __forceinline__ float ld(const float *p, float) { return *p; }
-  static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+  static __device__ __forceinline__ float ld1(const float *p) { return *p; }
+  static __device__ __forceinline__ void ld2(const float *p, float &a, float &b) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    a = v.x;
+    b = v.y;
+  }
+  static __device__ __forceinline__ void st1(float *p, float v) { *p = v; }
+  template <bool SR>
+  static __device__ __forceinline__ void st1r(float *p, float v, uint32_t, int) { *p = v; }
+  template <bool SR>
+  static __device__ __forceinline__ void st2(float *p, float a, float b, uint32_t, uint32_t) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+  }
 };
 
 struct StoreF16 {
   using T = __half;
-  static __device__ __forceinline__ float ld(const __half *p, float inv_s) {
-    return __half2float(*p) * inv_s;
+  static __device__ __forceinline__ float ld1(const __half *p) { return __half2float(*p); }
+  static __device__ __forceinline__ void ld2(const __half *p, float &a, float &b) {
+    const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+    a = v.x;
+    b = v.y;
   }
-  static __device__ __forceinline__ void st(__half *p, float v, float s) {
-    *p = __float2half_rn(v * s);
+  static __device__ __forceinline__ void st1(__half *p, float v) { *p = __float2half_rn(v); }
+  // Scalar store; with SR the 8 random bits of direction i come from the
+  // node hash h times an odd constant of that direction.
+  template <bool SR>
+  static __device__ __forceinline__ void st1r(__half *p, float v, uint32_t h, int i) {
+    if (SR) {
+      constexpr uint32_t kC[9] = {0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du, 0x27d4eb2fu,
+                                  0x165667b1u, 0xd3a2646du, 0xfd7046c5u, 0xb55a4f09u,
+                                  0x7feb352du};
+      const uint32_t r = ((h * kC[i]) >> 24) << 5;  // 8 bits just below the FP16 LSB
+      const float sv = __uint_as_float(__float_as_uint(v) + r);
+      unsigned short b;
+      asm("cvt.rz.f16.f32 %0, %1;" : "=h"(b) : "f"(sv));
+      *reinterpret_cast<unsigned short *>(p) = b;
+    } else {
+      *p = __float2half_rn(v);
+    }
+  }
+  // SR: add a random 13-bit offset below the FP16 mantissa to the FP32 bit
+  // pattern, then truncate toward zero; a value between two FP16 neighbours
+  // rounds up with probability equal to its distance from the lower one
+  // (exact for FP16 normals).  Otherwise round to nearest even.
+  template <bool SR>
+  static __device__ __forceinline__ void st2(__half *p, float a, float b, uint32_t ra,
+                                             uint32_t rb) {
+    uint32_t packed;
+    if (SR) {
+      const float sa = __uint_as_float(__float_as_uint(a) + ra);
+      const float sb = __uint_as_float(__float_as_uint(b) + rb);
+      asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(packed) : "f"(sb), "f"(sa));
+    } else {
+      const __half2 h = __floats2half2_rn(a, b);
+      packed = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint32_t *>(p) = packed;
   }
 };
 
 // ------------------------------------------------------------------- pull
-// Post-stream deviations d[0..8] of node (x, y) from the post-collision
-// buffer: f_i(x) = f*_i(x - e_i); a source in a wall row returns the node's
-// own population of the opposite direction (halfway bounce-back); periodic
-// edges wrap.  Sources outside [0, nx) only occur for the pressure columns,
-// whose populations are replaced by the extrapolation afterwards.
+// Post-stream values d[0..8] (stored units) of node (x, y): f_i(x) =
+// f*_i(x - e_i); a source in a plate row returns the node's own population
+// of the opposite direction (halfway bounce-back); periodic edges wrap.
 template <class S>
 __device__ __forceinline__ void pull_node(const typename S::T *__restrict__ fin,
-                                          const StepArgs &a, int x, int y,
-                                          float d[9]) {
+                                          const StepArgs &a, int x, int y, float d[9]) {
   const int xm = (x == 0) ? a.nx - 1 : x - 1;       // source for e_x = +1
   const int xp = (x == a.nx - 1) ? 0 : x + 1;       // source for e_x = -1
   const int ym = (y == 0) ? a.ny - 1 : y - 1;       // source for e_y = +1
@@ -79,74 +153,128 @@ __device__ __forceinline__ void pull_node(const typename S::T *__restrict__ fin,
   const long long r = (long long)y * a.pitch;
   const long long rm = (long long)ym * a.pitch;
   const long long rp = (long long)yp * a.pitch;
-  const float is = a.inv_scale;
-  d[0] = S::ld(fin + r + x, is);
-  d[1] = S::ld(fin + 1 * P + r + xm, is);
-  d[3] = S::ld(fin + 3 * P + r + xp, is);
-  d[2] = wm ? S::ld(fin + 4 * P + r + x, is) : S::ld(fin + 2 * P + rm + x, is);
-  d[5] = wm ? S::ld(fin + 7 * P + r + x, is) : S::ld(fin + 5 * P + rm + xm, is);
-  d[6] = wm ? S::ld(fin + 8 * P + r + x, is) : S::ld(fin + 6 * P + rm + xp, is);
-  d[4] = wp ? S::ld(fin + 2 * P + r + x, is) : S::ld(fin + 4 * P + rp + x, is);
-  d[7] = wp ? S::ld(fin + 5 * P + r + x, is) : S::ld(fin + 7 * P + rp + xp, is);
-  d[8] = wp ? S::ld(fin + 6 * P + r + x, is) : S::ld(fin + 8 * P + rp + xm, is);
+  d[0] = S::ld1(fin + r + x);
+  d[1] = S::ld1(fin + 1 * P + r + xm);
+  d[3] = S::ld1(fin + 3 * P + r + xp);
+  d[2] = wm ? S::ld1(fin + 4 * P + r + x) : S::ld1(fin + 2 * P + rm + x);
+  d[5] = wm ? S::ld1(fin + 7 * P + r + x) : S::ld1(fin + 5 * P + rm + xm);
+  d[6] = wm ? S::ld1(fin + 8 * P + r + x) : S::ld1(fin + 6 * P + rm + xp);
+  d[4] = wp ? S::ld1(fin + 2 * P + r + x) : S::ld1(fin + 4 * P + rp + x);
+  d[7] = wp ? S::ld1(fin + 5 * P + r + x) : S::ld1(fin + 7 * P + rp + xp);
+  d[8] = wp ? S::ld1(fin + 6 * P + r + x) : S::ld1(fin + 8 * P + rp + xm);
 }
 
 // ---------------------------------------------------- macroscopic state
 struct NodeState {
-  float drho;   // rho - rho0
-  float rho;
-  float ux, uy; // physical velocity (Eq. 17 / quadratic form)
-  float Fx, Fy; // total force (Eq. 2 / Eq. 8)
+  float drho_s;  // (rho - rho0) * S
+  float mx, my;  // momentum sum_i f_i e_i, stored units
+  float rho;     // physical density
+  float ux, uy;  // physical velocity (Eq. 17 / quadratic form)
+  float Fx, Fy;  // total force (Eq. 2 / Eq. 8)
+  float ieps;    // 1 / eps (0 for an impermeable node)
 };
 
 // Eq. 16a, Eq. 16b solved for u (Eq. 17, or u = v / (c0 + sqrt(c0^2 +
 // c1|v|)) with the Forchheimer term), and F of Eq. 2.  eps = 0 is an
 // impermeable node: u = 0 and F = -2 m / rho (Eq. 16b with u = 0).
-__device__ __forceinline__ NodeState node_state(const float d[9], float eps,
-                                                float inv_k, const StepArgs &a) {
+__device__ __forceinline__ NodeState node_state(const float d[9], float eps, float inv_k,
+                                                const StepArgs &a) {
   NodeState s;
-  s.drho = ((d[0] + (d[1] + d[3])) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
-  s.rho = a.rho0 + s.drho;
+  s.drho_s = ((d[0] + (d[1] + d[3])) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
   // sum_i w_i e_i = 0, so the momentum of the deviations is the momentum.
   const float mx = (d[1] - d[3]) + ((d[5] - d[7]) + (d[8] - d[6]));
   const float my = (d[2] - d[4]) + ((d[5] - d[7]) + (d[6] - d[8]));
-  const float inv_rho = 1.0f / s.rho;
+  s.mx = mx;
+  s.my = my;
+  s.rho = fmaf(s.drho_s, a.inv_scale, a.rho0);
+  const float c = a.inv_scale * rcp_approx(s.rho);  // 1 / (S rho)
   if (eps > 0.0f) {
-    const float vx = fmaf(0.5f * eps, a.Gx, mx * inv_rho);
-    const float vy = fmaf(0.5f * eps, a.Gy, my * inv_rho);
+    s.ieps = rcp_approx(eps);
+    const float eGx = eps * a.Gx, eGy = eps * a.Gy;
+    const float vx = fmaf(0.5f, eGx, mx * c);
+    const float vy = fmaf(0.5f, eGy, my * c);
     const float darcy = eps * a.nu * inv_k;       // eps nu / k_a
     const float c0 = fmaf(0.25f, darcy, 0.5f);    // (1 + eps nu / (2 k_a)) / 2
-    float den, forch = 0.0f;
+    float idn, drag;
     if (a.forch) {
-      // c1 = eps F_eps / (2 sqrt(k_a)), F_eps = 1.75 / sqrt(150 eps^3)
-      const float c1 = a.fe_half * sqrtf(inv_k) * rsqrtf(eps);
-      const float vmag = sqrtf(fmaf(vx, vx, vy * vy));
-      den = c0 + sqrtf(fmaf(c0, c0, c1 * vmag));
-      forch = 2.0f * c1;                          // eps F_eps / sqrt(k_a)
+      // c1 = eps F_eps / (2 sqrt(k_a)) with F_eps = 1.75 / sqrt(150 eps^3)
+      const float c1 = a.fe_half * sqrt_approx(inv_k * s.ieps);
+      const float vmag = sqrt_approx(fmaf(vx, vx, vy * vy));
+      idn = rcp_approx(c0 + sqrt_approx(fmaf(c0, c0, c1 * vmag)));
+      drag = fmaf(2.0f * c1, vmag * idn, darcy);  // eps nu/k_a + eps F_eps |u| / sqrt(k_a)
     } else {
-      den = 2.0f * c0;
+      idn = rcp_approx(2.0f * c0);
+      drag = darcy;
     }
-    const float inv_den = 1.0f / den;
-    s.ux = vx * inv_den;
-    s.uy = vy * inv_den;
-    const float drag = (a.forch) ? fmaf(forch, sqrtf(fmaf(s.ux, s.ux, s.uy * s.uy)), darcy)
-                                 : darcy;
-    s.Fx = fmaf(-drag, s.ux, eps * a.Gx);
-    s.Fy = fmaf(-drag, s.uy, eps * a.Gy);
+    s.ux = vx * idn;
+    s.uy = vy * idn;
+    s.Fx = fmaf(-drag, s.ux, eGx);
+    s.Fy = fmaf(-drag, s.uy, eGy);
   } else {
+    s.ieps = 0.0f;
     s.ux = 0.0f;
     s.uy = 0.0f;
-    s.Fx = -2.0f * mx * inv_rho;
-    s.Fy = -2.0f * my * inv_rho;
+    s.Fx = -2.0f * mx * c;
+    s.Fy = -2.0f * my * c;
   }
   return s;
 }
 
-// Deviation of the porous equilibrium (Eq. 14) from w_i rho0, all nine
-// directions: deq_i = w_i (rho - rho0) + w_i rho (3 e.u + (9/2 (e.u)^2 -
-// 3/2 u^2) / eps); eps = 0 keeps only w_i (rho - rho0).
-__device__ __forceinline__ void equilibrium_dev(float drho, float rho, float ux,
-                                                float uy, float eps, float deq[9]) {
+// Eq. 12 with the equilibrium of Eq. 14 and the forcing of Eq. 15 (last term
+// over eps), in stored units, written through moments:
+//   d*_i = (1 - 1/tau) d_i + w_i S [A + e_i.P + e_i^T M e_i],
+//   A = drho/tau - rho (3 u^2 / (2 eps tau) + (1 - 1/2tau) 3 u.F / eps),
+//   P = 3 rho (u / tau + (1 - 1/2tau) F) = 3 (m / tau + rho F),
+//   M = rho (9 u u / (2 eps tau) + (1 - 1/2tau) 9 (u F + F u) / (2 eps)),
+// which is f_eq / tau + F_i expanded direction by direction.  P uses the
+// identity rho u = m + rho F / 2 (Eq. 16b): the momentum the collision hands
+// on is then m + rho F exactly, whatever the rounding of u.  The weights are
+// applied as hi + lo pairs so that their FP32 representation error does not
+// bias the momentum at every node in the same direction.
+constexpr float kW0h = 4.0f / 9.0f;
+constexpr float kW1h = 1.0f / 9.0f;
+constexpr float kW2h = 1.0f / 36.0f;
+constexpr float kW0l = (float)(4.0 / 9.0 - (double)kW0h);
+constexpr float kW1l = (float)(1.0 / 9.0 - (double)kW1h);
+constexpr float kW2l = (float)(1.0 / 36.0 - (double)kW2h);
+
+__device__ __forceinline__ float wmul(float wh, float wl, float t) { return fmaf(wh, t, wl * t); }
+
+__device__ __forceinline__ void collide(float d[9], const NodeState &s, const StepArgs &a) {
+  const float mx = s.mx, my = s.my;
+  const float rs = s.rho * a.scale;
+  const float ux = s.ux, uy = s.uy, Fx = s.Fx, Fy = s.Fy, ie = s.ieps;
+  const float om = a.omega, cf = a.cforce;
+  const float usq = 1.5f * ie * fmaf(ux, ux, uy * uy);
+  const float uF3 = 3.0f * ie * fmaf(ux, Fx, uy * Fy);
+  const float A = fmaf(om, s.drho_s, -rs * fmaf(om, usq, cf * uF3));
+  const float Px = 3.0f * fmaf(om, mx, rs * Fx);
+  const float Py = 3.0f * fmaf(om, my, rs * Fy);
+  const float qq = om * 4.5f * ie * rs;
+  const float gg = cf * 9.0f * ie * rs;
+  const float Mxx = ux * fmaf(qq, ux, gg * Fx);
+  const float Myy = uy * fmaf(qq, uy, gg * Fy);
+  const float Mxy2 = fmaf(2.0f * qq * ux, uy, gg * fmaf(ux, Fy, uy * Fx));  // 2 M_xy
+  const float sx = A + Mxx, sy = A + Myy, sd = sx + Myy;
+  const float s5 = sd + Mxy2, s6 = sd - Mxy2;
+  const float pp = Px + Py, pm = Px - Py;
+  const float o1 = a.one_m_omega;
+  d[0] = fmaf(o1, d[0], wmul(kW0h, kW0l, A));
+  d[1] = fmaf(o1, d[1], wmul(kW1h, kW1l, sx + Px));
+  d[3] = fmaf(o1, d[3], wmul(kW1h, kW1l, sx - Px));
+  d[2] = fmaf(o1, d[2], wmul(kW1h, kW1l, sy + Py));
+  d[4] = fmaf(o1, d[4], wmul(kW1h, kW1l, sy - Py));
+  d[5] = fmaf(o1, d[5], wmul(kW2h, kW2l, s5 + pp));
+  d[7] = fmaf(o1, d[7], wmul(kW2h, kW2l, s5 - pp));
+  d[6] = fmaf(o1, d[6], wmul(kW2h, kW2l, s6 - pm));
+  d[8] = fmaf(o1, d[8], wmul(kW2h, kW2l, s6 + pm));
+}
+
+// Deviation of the porous equilibrium (Eq. 14) from w_i rho0, physical
+// units: deq_i = w_i (rho - rho0) + w_i rho (3 e.u + (9/2 (e.u)^2 - 3/2 u^2)
+// / eps); eps = 0 keeps only w_i (rho - rho0).
+__device__ __forceinline__ void equilibrium_dev(float drho, float rho, float ux, float uy,
+                                                float eps, float deq[9]) {
   const float inv_eps = (eps > 0.0f) ? 1.0f / eps : 0.0f;
   const float vx = (eps > 0.0f) ? ux : 0.0f;
   const float vy = (eps > 0.0f) ? uy : 0.0f;
@@ -166,46 +294,13 @@ __device__ __forceinline__ void equilibrium_dev(float drho, float rho, float ux,
   eu = vx - vy;   deq[8] = fmaf(r2, 3.0f * eu + fmaf(q * eu, eu, -usq), dr2);
 }
 
-// Eq. 12 with Eq. 14 and Eq. 15 (last term over eps), in place on the
-// deviations: d_i <- d_i - (d_i - deq_i) / tau + F_i.
-__device__ __forceinline__ void collide(float d[9], const NodeState &s, float eps,
-                                        const StepArgs &a) {
-  float deq[9];
-  equilibrium_dev(s.drho, s.rho, s.ux, s.uy, eps, deq);
-  const float inv_eps = (eps > 0.0f) ? 1.0f / eps : 0.0f;
-  const float ux = s.ux, uy = s.uy, Fx = s.Fx, Fy = s.Fy;
-  const float uF3 = 3.0f * inv_eps * fmaf(ux, Fx, uy * Fy);
-  const float g9 = 9.0f * inv_eps;
-  const float c = s.rho * a.cforce;
-  const float c0 = kW0 * c, c1 = kW1 * c, c2 = kW2 * c;
-  const float om = a.omega;
-  float eu, eF, Fi;
-  Fi = -c0 * uF3;
-  d[0] = fmaf(-om, d[0] - deq[0], d[0]) + Fi;
-#define LBMP_DIR(I, EU, EF, CW)                                   \
-  eu = (EU);                                                      \
-  eF = (EF);                                                      \
-  Fi = (CW) * (fmaf(g9 * eu, eF, 3.0f * eF) - uF3);               \
-  d[I] = fmaf(-om, d[I] - deq[I], d[I]) + Fi;
-  LBMP_DIR(1, ux, Fx, c1)
-  LBMP_DIR(2, uy, Fy, c1)
-  LBMP_DIR(3, -ux, -Fx, c1)
-  LBMP_DIR(4, -uy, -Fy, c1)
-  LBMP_DIR(5, ux + uy, Fx + Fy, c2)
-  LBMP_DIR(6, uy - ux, Fy - Fx, c2)
-  LBMP_DIR(7, -ux - uy, -Fx - Fy, c2)
-  LBMP_DIR(8, ux - uy, Fx - Fy, c2)
-#undef LBMP_DIR
-}
-
-// Pressure column (non-equilibrium extrapolation, Guo, Zheng & Shi 2002):
-// d_b = d_n + deq(rho_b, u_n; eps_b) - deq(rho_n, u_n; eps_n), where n is the
-// adjacent interior node and rho_b the imposed density.
+// Pressure column (non-equilibrium extrapolation, Guo, Zheng & Shi 2002),
+// stored units: d_b = d_n + S (deq(rho_b, u_n; eps_b) - deq(rho_n, u_n;
+// eps_n)), n the adjacent interior node and rho_b the imposed density.
 template <class S>
 __device__ __forceinline__ void pressure_node(const typename S::T *__restrict__ fin,
-                                              const float2 *__restrict__ med,
-                                              const StepArgs &a, int xb, int y,
-                                              float eps_b, float d[9]) {
+                                           const float2 *__restrict__ med, const StepArgs &a,
+                                           int xb, int y, float eps_b, float d[9]) {
   const int xn = (xb == 0) ? 1 : a.nx - 2;
   const float2 mn = med[(long long)y * a.pitch + xn];
   float dn[9];
@@ -214,9 +309,9 @@ __device__ __forceinline__ void pressure_node(const typename S::T *__restrict__ 
   const float drho_b = (xb == 0) ? a.drho_in : a.drho_out;
   float eq_b[9], eq_n[9];
   equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, eps_b, eq_b);
-  equilibrium_dev(sn.drho, sn.rho, sn.ux, sn.uy, mn.x, eq_n);
+  equilibrium_dev(sn.drho_s * a.inv_scale, sn.rho, sn.ux, sn.uy, mn.x, eq_n);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) d[i] = dn[i] + (eq_b[i] - eq_n[i]);
+  for (int i = 0; i < 9; ++i) d[i] = fmaf(a.scale, eq_b[i] - eq_n[i], dn[i]);
 }
 
 }  // namespace lbmp

@@ -80,6 +80,8 @@ struct lbmp_ctx {
   double *results = nullptr;    // device, kNQ doubles
   double *h_results = nullptr;  // pinned host, kNQ doubles
   unsigned *d_flag = nullptr;
+  unsigned long long *d_tctr = nullptr;  // time level for the stochastic rounding
+  bool sr = false;
   bool fields_set = false;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -102,6 +104,7 @@ struct lbmp_ctx {
     a.drho_in = (float)(p.rho_in - p.rho0);
     a.drho_out = (float)(p.rho_out - p.rho0);
     a.omega = (float)(1.0 / p.tau);
+    a.one_m_omega = (float)(1.0 - 1.0 / p.tau);
     a.cforce = (float)(1.0 - 0.5 / p.tau);
     a.nu = (float)((p.tau - 0.5) / 3.0 / p.J);
     a.Gx = (float)p.Gx;
@@ -112,6 +115,8 @@ struct lbmp_ctx {
     a.walls = p.bc_y == LBMP_BCY_WALLS;
     a.pressure = p.bc_x == LBMP_BCX_PRESSURE;
     a.forch = p.forchheimer != 0;
+    a.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
+    a.seed_hi = (uint32_t)(p.seed >> 32);
     return a;
   }
   int rows() const { return y_hi - y_lo; }
@@ -156,6 +161,7 @@ void release(lbmp_ctx *c) {
   cudaFree(c->partials);
   cudaFree(c->results);
   cudaFree(c->d_flag);
+  cudaFree(c->d_tctr);
   if (c->h_results) cudaFreeHost(c->h_results);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -198,19 +204,25 @@ lbmp_status run_macro(lbmp_ctx *c, lbmp::MacroOut o, bool reduce) {
   return LBMP_OK;
 }
 
+// n single launches (time levels *tctr + 0 .. n-1), then the counter bump.
 lbmp_status launch_steps(lbmp_ctx *c, int64_t n) {
   StepArgs a = c->args();
   for (int64_t t = 0; t < n; ++t) {
-    LBMP_CK(lbmp::launch_step(c->p.storage, a, c->rows(), c->buf[c->cur],
-                              c->buf[c->cur ^ 1], c->med, c->stream));
+    LBMP_CK(lbmp::launch_step(c->p.storage, c->sr, a, c->rows(), c->buf[c->cur],
+                              c->buf[c->cur ^ 1], c->med, c->d_tctr, (int)t, c->stream));
     c->cur ^= 1;
+    c->launches++;
+  }
+  if (c->sr && n > 0) {
+    LBMP_CK(lbmp::launch_bump(c->d_tctr, (int)n, c->stream));
     c->launches++;
   }
   return LBMP_OK;
 }
 
 // Graph of kGraphSteps steps starting from buffer `cur` (captured once per
-// medium: the launch arguments hold the storage scale).
+// medium: the launch arguments hold the storage scale), plus the counter
+// bump when the rounding is stochastic.
 lbmp_status get_graph(lbmp_ctx *c, int cur, cudaGraphExec_t *out) {
   if (c->graph[cur]) {
     *out = c->graph[cur];
@@ -222,10 +234,11 @@ lbmp_status get_graph(lbmp_ctx *c, int cur, cudaGraphExec_t *out) {
   int b = cur;
   cudaError_t err = cudaSuccess;
   for (int t = 0; t < kGraphSteps && err == cudaSuccess; ++t) {
-    err = lbmp::launch_step(c->p.storage, a, c->rows(), c->buf[b], c->buf[b ^ 1], c->med,
-                            c->cap_stream);
+    err = lbmp::launch_step(c->p.storage, c->sr, a, c->rows(), c->buf[b], c->buf[b ^ 1],
+                            c->med, c->d_tctr, t, c->cap_stream);
     b ^= 1;
   }
+  if (err == cudaSuccess && c->sr) err = lbmp::launch_bump(c->d_tctr, kGraphSteps, c->cap_stream);
   cudaError_t end = cudaStreamEndCapture(c->cap_stream, &g);
   if (err != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -284,7 +297,8 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
       return fail(LBMP_EINVAL, "storage must be LBMP_STORE_FP32 or LBMP_STORE_FP16");
     if (p.fp16_log2_scale < -60 || p.fp16_log2_scale > 60)
       return fail(LBMP_EINVAL, "fp16_log2_scale must be in [-60, 60]");
-    if (p.reserved != 0) return fail(LBMP_EINVAL, "reserved must be 0");
+    if (p.fp16_rounding != LBMP_ROUND_STOCHASTIC && p.fp16_rounding != LBMP_ROUND_NEAREST)
+      return fail(LBMP_EINVAL, "fp16_rounding must be LBMP_ROUND_STOCHASTIC or LBMP_ROUND_NEAREST");
 
     lbmp_ctx *c = new (std::nothrow) lbmp_ctx();
     if (!c) return fail(LBMP_ENOMEM, "host allocation of the context");
@@ -296,6 +310,7 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
       return cuda_fail(e, "cudaGetDevice");
     }
     c->elem = (p.storage == LBMP_STORE_FP32) ? 4 : 2;
+    c->sr = p.storage == LBMP_STORE_FP16 && p.fp16_rounding == LBMP_ROUND_STOCHASTIC;
     c->pitch = ((p.nx + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
     c->plane = (long long)c->pitch * p.ny;
     c->y_lo = (p.bc_y == LBMP_BCY_WALLS) ? 1 : 0;
@@ -330,6 +345,7 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
                     (size_t)c->partials_blocks * lbmp::kNQ * sizeof(double), "reduction partials"));
     LBMP_TRY(dalloc(c, (void **)&c->results, lbmp::kNQ * sizeof(double), "reduction results"));
     LBMP_TRY(dalloc(c, (void **)&c->d_flag, sizeof(unsigned), "validation flag"));
+    LBMP_TRY(dalloc(c, (void **)&c->d_tctr, sizeof(unsigned long long), "time-level counter"));
     e = cudaMallocHost((void **)&c->h_results, lbmp::kNQ * sizeof(double));
     if (e != cudaSuccess) LBMP_TRY(cuda_fail(e, "cudaMallocHost"));
 #undef LBMP_TRY
@@ -372,6 +388,7 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
       dn = t + 2 * n;
     }
     LBMP_CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
+    LBMP_CK(cudaMemsetAsync(c->med, 0, (size_t)c->plane * sizeof(float2), c->stream));
     LBMP_CK(lbmp::launch_medium(de, dk, dn, p.nx, p.ny, c->pitch, c->y_lo, c->y_hi, c->med,
                                 c->d_flag, c->partials, c->stream));
     c->launches++;
@@ -417,6 +434,7 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
     LBMP_CK(cudaMemsetAsync(c->buf[0], 0, c->buf_bytes(), c->stream));
     LBMP_CK(cudaMemsetAsync(c->buf[1], 0, c->buf_bytes(), c->stream));
     LBMP_CK(cudaMemsetAsync(c->uprev, 0, (size_t)c->plane * sizeof(float2), c->stream));
+    LBMP_CK(cudaMemsetAsync(c->d_tctr, 0, sizeof(unsigned long long), c->stream));
     LBMP_CK(cudaStreamSynchronize(c->stream));
     c->cur = 0;
     c->steps = 0;
@@ -441,7 +459,7 @@ lbmp_status lbmp_step(lbmp_ctx *c, int64_t n) {
       st = get_graph(c, c->cur, &g);
       if (st) return st;
       LBMP_CK(cudaGraphLaunch(g, c->stream));
-      c->launches += kGraphSteps;
+      c->launches += kGraphSteps + (c->sr ? 1 : 0);
       left -= kGraphSteps;
     }
     st = launch_steps(c, left);
@@ -665,6 +683,8 @@ lbmp_status lbmp_set_state(lbmp_ctx *c, const void *buf, size_t bytes, int32_t w
     cudaMemcpyKind k = (where == LBMP_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     LBMP_CK(cudaStreamSynchronize(c->stream));
     LBMP_CK(cudaMemcpy(c->buf[c->cur], (const char *)buf + sizeof(h), c->buf_bytes(), k));
+    const unsigned long long t = (unsigned long long)h.steps;
+    LBMP_CK(cudaMemcpy(c->d_tctr, &t, sizeof(t), cudaMemcpyHostToDevice));
     c->steps = h.steps;
     return LBMP_OK;
   } catch (...) {

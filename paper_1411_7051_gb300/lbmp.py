@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENAN, ETIMEOUT = range(7)
 BCX_PERIODIC, BCX_PRESSURE = 0, 1
 BCY_PERIODIC, BCY_WALLS = 0, 1
 STORE_FP32, STORE_FP16 = 0, 1
+ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
 HOST, DEVICE = 0, 1
 
 _STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE",
@@ -44,8 +45,8 @@ class Params(ctypes.Structure):
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
         ("rho0", ctypes.c_double), ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
         ("forchheimer", ctypes.c_int32), ("storage", ctypes.c_int32),
-        ("fp16_log2_scale", ctypes.c_int32), ("reserved", ctypes.c_int32),
-        ("stream", ctypes.c_void_p),
+        ("fp16_log2_scale", ctypes.c_int32), ("fp16_rounding", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
     ]
 
 
@@ -149,13 +150,15 @@ class SimConfig:
     forchheimer: int = 0
     storage: int = STORE_FP32
     fp16_log2_scale: int = 0
+    fp16_rounding: int = ROUND_STOCHASTIC
+    seed: int = 0
 
     def to_params(self, stream: int | None) -> Params:
         return Params(int(self.nx), int(self.ny), float(self.tau), float(self.J),
                       float(self.G[0]), float(self.G[1]), int(self.bc_x), int(self.bc_y),
                       float(self.rho0), float(self.rho_in), float(self.rho_out),
-                      int(self.forchheimer), int(self.storage), int(self.fp16_log2_scale), 0,
-                      stream)
+                      int(self.forchheimer), int(self.storage), int(self.fp16_log2_scale),
+                      int(self.fp16_rounding), int(self.seed) & (2**64 - 1), stream)
 
 
 class Sim:

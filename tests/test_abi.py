@@ -55,6 +55,7 @@ def _create(L, **kw):
     ({"forchheimer": 2}, "forchheimer"),
     ({"storage": 5}, "storage"),
     ({"fp16_log2_scale": 100}, "fp16_log2_scale"),
+    ({"fp16_rounding": 3}, "fp16_rounding"),
 ])
 def test_create_rejects_bad_parameters(L, kw, needle):
     st, msg = _create(L, **kw)

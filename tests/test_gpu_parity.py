@@ -3,10 +3,24 @@ inputs.  Tolerances:
 
 * one step from the same state, FP32 storage: populations within 2e-9
   absolute (FP32 rounding of O(1e-3) deviations and of rho);
-* many steps, FP32: relative L2 of the velocity <= 1e-5 and global
+* steady states, FP32: relative L2 of the velocity <= 1e-5 and global
   permeability <= 1e-6 relative;
-* FP16-stored populations: global permeability <= 1e-3 relative.
+* transient states of pressure-driven runs, FP32: relative L2 of the
+  velocity <= 1e-5 and global permeability <= 1e-5.  While the pressure
+  wave crosses the lattice the stored deviations f_i - w_i rho0 carry the
+  density deviation (up to 5e-4), about 1e3 times the velocity signal, so
+  one FP32 rounding (2^-24) moves the velocity of a node by ~1e-4 relative
+  per step; the domain mean averages this to ~1e-6 and the bound keeps a
+  factor 10;
+* FP16-stored populations (stochastic rounding, the default): global
+  permeability <= 1e-3 relative; one step from the same state: each
+  population within one FP16 ulp of its deviation (2^-10 relative).
+
+Measured errors are appended to $LBMP_PARITY_LOG (JSON lines) when set.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +30,7 @@ from helpers import Case, fluid_rows, gpu_sim, oracle_sim, rel_l2
 pytestmark = pytest.mark.gpu
 
 FP32, FP16 = 0, 1
+SR, RN = 0, 1
 
 
 def _np(t):
@@ -32,9 +47,18 @@ def _compare_velocity(gs, osim, case, rel_u=1e-5, rel_k=1e-6):
     kg_g, _ = gs.permeability()
     kg_o, _ = osim.permeability()
     e_k = abs(kg_g / kg_o - 1)
+    _log(e_u=e_u, e_k=e_k, kg=kg_g, kg_oracle=kg_o)
     assert e_u <= rel_u, f"rel-L2(u) = {e_u:.3e}"
     assert e_k <= rel_k, f"k_g rel err = {e_k:.3e} ({kg_g} vs {kg_o})"
     return e_u, e_k
+
+
+def _log(**kw):
+    path = os.environ.get("LBMP_PARITY_LOG")
+    if path:
+        kw["test"] = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+        with open(path, "a") as fh:
+            fh.write(json.dumps(kw) + "\n")
 
 
 # ----------------------------------------------------- one step, elementwise
@@ -73,6 +97,38 @@ def test_one_step_from_random_state(orc, name, nx, ny):
                                    osim.populations()[:, fr], rtol=0, atol=2e-9)
 
 
+@pytest.mark.parametrize("rounding", [SR, RN])
+def test_one_step_fp16_within_one_ulp(orc, rounding):
+    nx, ny = 130, 21
+    med = media.random_medium(nx, ny, seed=5, p_open=0.1, p_solid=0.1, log10_k_range=(-3, 0))
+    case = Case(nx, ny, tau=0.75, G=(2e-5, 0.0), walls=True, pressure=True, rho_in=1.001,
+                rho_out=0.999, forchheimer=1, medium=med)
+    _, _, w = orc.lattice()
+    f0 = media.random_populations(nx, ny, seed=8, base=w, amp=2e-3)
+    osim = oracle_sim(orc, case)
+    gs = gpu_sim(case, FP16, fp16_rounding=rounding)
+    gs.set_populations(f0)
+    # start both from the FP16-rounded state the GPU holds
+    osim.set_populations(_np(gs.populations()))
+    fr = fluid_rows(case)
+    wb = w[:, None, None]
+    for _ in range(2):
+        osim.step(1)
+        gs.step(1)
+        fo = osim.populations()[:, fr]
+        dev = np.abs(fo - wb)
+        err = np.abs(_np(gs.populations())[:, fr] - fo)
+        # interior columns: one FP16 rounding of the node's own deviation
+        inner = (slice(None), slice(None), slice(1, nx - 1))
+        assert np.all(err[inner] <= dev[inner] * 2.0 ** -10 + 1e-10), err[inner].max()
+        # pressure columns are extrapolated from their neighbour and inherit
+        # its rounding: bound by the neighbour's deviation
+        for xb, xn in ((0, 1), (nx - 1, nx - 2)):
+            bound = 2.0 * dev[:, :, xn].max(axis=0) * 2.0 ** -10 + 1e-10
+            assert np.all(err[:, :, xb] <= bound[None, :]), err[:, :, xb].max()
+        osim.set_populations(_np(gs.populations()))
+
+
 # --------------------------------------------- validation channel (config 1)
 def test_channel_validation_config(orc):
     """64 x 33 channel, eps 0.7, tau 0.8, Da 1e-3, Kn 0.1, G 1e-6 (FP64 oracle
@@ -109,10 +165,14 @@ def test_two_component_fp32(orc, kn):
     for n in (100, 900):
         osim.step(n)
         gs.step(n)
-    _compare_velocity(gs, osim, case)
+    _compare_velocity(gs, osim, case, rel_k=1e-5)
 
 
 def test_forchheimer_shale_fp32(orc):
+    """Fractured shale, transient.  Matrix velocities (k_i ~ 1e-6) are ~1e-9
+    under a density deviation of ~1e-3, so FP32 carries them with a few
+    significant digits only; the fracture velocities dominate the L2 norm.
+    Velocity bound 2e-5 (measured ~1.1e-5), permeability 1e-5."""
     med = media.shale_fractures(n=160, seed=5, n_fractures=4, length=(40, 120))
     case = Case(160, 160, tau=0.9, pressure=True, walls=False, rho_in=1.001,
                 rho_out=0.999, forchheimer=1, medium=med)
@@ -120,7 +180,7 @@ def test_forchheimer_shale_fp32(orc):
     gs = gpu_sim(case, FP32)
     osim.step(600)
     gs.step(600)
-    _compare_velocity(gs, osim, case)
+    _compare_velocity(gs, osim, case, rel_u=2e-5, rel_k=1e-5)
 
 
 def test_impermeable_and_open_nodes_fp32(orc):
@@ -134,28 +194,65 @@ def test_impermeable_and_open_nodes_fp32(orc):
     _compare_velocity(gs, osim, case)
 
 
+# ---------------------------------------------- heterogeneous steady states
+def _steady_cases():
+    body = Case(64, 48, tau=0.8, G=(2e-6, 5e-7), walls=True, forchheimer=1,
+                medium=media.random_medium(64, 48, seed=31, eps_range=(0.3, 1.0),
+                                           log10_k_range=(-1, 1), kn_range=(0, 2),
+                                           p_open=0.1))
+    pres = Case(48, 32, tau=0.8, pressure=True, walls=True, rho_in=1.0005, rho_out=0.9995,
+                medium=media.two_component(48, seed=7, corr_len=6.0, kn=0.5, ny=32,
+                                           matrix=(0.4, 0.1), inclusion=(0.8, 1.0)))
+    return {"body_force_random": body, "pressure_two_component": pres}
+
+
+@pytest.mark.parametrize("name", ["body_force_random", "pressure_two_component"])
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_heterogeneous_steady_state(orc, name, storage):
+    case = _steady_cases()[name]
+    osim = oracle_sim(orc, case)
+    osim.run_to_steady(tol=1e-10, check_every=200, max_steps=400_000)
+    gs = gpu_sim(case, storage)
+    gs.step(osim.steps)
+    if storage == FP32:
+        _compare_velocity(gs, osim, case)
+    else:
+        kg_g, _ = gs.permeability()
+        kg_o, _ = osim.permeability()
+        _log(e_k=abs(kg_g / kg_o - 1), kg=kg_g, kg_oracle=kg_o, storage="fp16")
+        assert abs(kg_g / kg_o - 1) <= 1e-3, (kg_g, kg_o)
+
+
 # ------------------------------------------------------------- FP16 storage
-def test_fp16_channel_permeability(orc):
+@pytest.mark.parametrize("rounding", [SR, RN])
+def test_fp16_channel_permeability(orc, rounding):
+    """Steady channel.  Round-to-nearest repeats the same rounding error at
+    every step of a steady state, which the weak damping (eps nu / k_a =
+    0.05 per step) amplifies about 20-fold: measured ~3e-3.  Stochastic
+    rounding makes the error zero-mean in time: ~1e-5."""
     med = media.channel(64, 33, 0.7, 1e-3, 0.1)
     case = Case(64, 33, tau=0.8, G=(1e-6, 0.0), walls=True, medium=med)
     osim = oracle_sim(orc, case)
     osim.run_to_steady(tol=1e-10, check_every=100)
-    gs = gpu_sim(case, FP16)
+    gs = gpu_sim(case, FP16, fp16_rounding=rounding)
     gs.step(max(osim.steps, 2000))
     kg_g, _ = gs.permeability()
     kg_o, _ = osim.permeability()
-    assert abs(kg_g / kg_o - 1) <= 1e-3, (kg_g, kg_o)
+    _log(e_k=abs(kg_g / kg_o - 1), kg=kg_g, kg_oracle=kg_o, storage="fp16",
+         rounding="SR" if rounding == SR else "RN")
+    assert abs(kg_g / kg_o - 1) <= (1e-3 if rounding == SR else 1e-2), (kg_g, kg_o)
 
 
 @pytest.mark.parametrize("kn", [0.01, 1.0])
 def test_fp16_two_component_permeability(orc, kn):
     case = _two_component_case(kn=kn)
     osim = oracle_sim(orc, case)
-    gs = gpu_sim(case, FP16)
+    gs = gpu_sim(case, FP16, fp16_rounding=SR)
     osim.step(1000)
     gs.step(1000)
     kg_g, _ = gs.permeability()
     kg_o, _ = osim.permeability()
+    _log(e_k=abs(kg_g / kg_o - 1), kg=kg_g, kg_oracle=kg_o, storage="fp16")
     assert abs(kg_g / kg_o - 1) <= 1e-3, (kg_g, kg_o)
 
 
@@ -170,10 +267,11 @@ def test_mass_conservation_gpu(orc):
     assert abs(m1 / m0 - 1) < 1e-9, (m0, m1)
 
 
-def test_graph_replay_matches_single_launches():
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_graph_replay_matches_single_launches(storage):
     case = _two_component_case(n=200, ny=50)
-    a = gpu_sim(case, FP32)
-    b = gpu_sim(case, FP32)
+    a = gpu_sim(case, storage)
+    b = gpu_sim(case, storage)
     a.step(70)            # two graph replays + 6 single launches
     for _ in range(70):
         b.step(1)
@@ -192,6 +290,18 @@ def test_checkpoint_restart_bitwise(storage):
     assert b.info().steps == 50
     b.step(50)
     assert np.array_equal(_np(a.populations()), _np(b.populations()))
+
+
+def test_stochastic_rounding_is_seeded():
+    case = _two_component_case(n=96, ny=40)
+    a = gpu_sim(case, FP16, seed=7)
+    b = gpu_sim(case, FP16, seed=7)
+    c = gpu_sim(case, FP16, seed=8)
+    for s_ in (a, b, c):
+        s_.step(40)
+    fa, fb, fc = (_np(s_.populations()) for s_ in (a, b, c))
+    assert np.array_equal(fa, fb)
+    assert not np.array_equal(fa, fc)
 
 
 def test_residual_semantics():
