@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--kernel", choices=["auto", "staged", "direct"], default="auto",
+                    help="implementation of the step kernel (auto: direct for FP32 storage, "
+                         "staged for FP16)")
     return ap.parse_args()
 
 
@@ -217,11 +220,13 @@ def config_dict(args, cfg, storage):
 
 
 # ------------------------------------------------------------- GPU (ours)
-def time_storage(lbmp, torch, med, cfg, storage, K, W):
+def time_storage(lbmp, torch, med, cfg, storage, K, W, kernel):
     st = lbmp.STORE_FP32 if storage == "fp32" else lbmp.STORE_FP16
     sc = lbmp.SimConfig(cfg["nx"], cfg["ny"], tau=cfg["tau"], bc_x=cfg["bc_x"],
                         bc_y=cfg["bc_y"], rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
-                        forchheimer=cfg["forchheimer"], storage=st)
+                        forchheimer=cfg["forchheimer"], storage=st,
+                        kernel={"auto": lbmp.KERNEL_AUTO, "staged": lbmp.KERNEL_STAGED,
+                                "direct": lbmp.KERNEL_DIRECT}[kernel])
     sim = lbmp.Sim(sc)
     sim.set_fields(med.eps, med.k_i, med.kn)
     sim.step(W)
@@ -269,6 +274,11 @@ def time_e2e(lbmp, torch, med, cfg, K):
     return dict(s=dt, h2d=3 * 8 * n, d2h=6 * 8 + 4)
 
 
+def kernel_name(kernel: str, tag: str) -> str:
+    staged = kernel == "staged" or (kernel == "auto" and tag == "StoreF16")
+    return f"lbmp::staged_step_kernel<{tag}>" if staged else f"lbmp::step_kernel<{tag}>"
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_1411_7051_gb300 import build as lbuild, lbmp
@@ -284,11 +294,11 @@ def run_ours(args, ws, rank, local):
     other = "fp16" if primary == "fp32" else "fp32"
 
     with ClockSampler(local) as clk:
-        res = time_storage(lbmp, torch, med, cfg, primary, K, W)
+        res = time_storage(lbmp, torch, med, cfg, primary, K, W, args.kernel)
     clocks = clk.summary()
     res_other = None
     if not args.no_other:
-        res_other = time_storage(lbmp, torch, med, cfg, other, K, W)
+        res_other = time_storage(lbmp, torch, med, cfg, other, K, W, args.kernel)
     e2e = None if args.no_e2e else time_e2e(lbmp, torch, med, cfg, K)
 
     # slowest rank decides
@@ -321,13 +331,13 @@ def run_ours(args, ws, rank, local):
                 "bytes_per_update": r["bpu"],
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
                 "traffic_per_update": (tr["dram_bytes_per_launch"] / r["nodes"] if tr else None),
-                "kernel": f"lbmp::step_kernel<{tag}>"}
+                "kernel": kernel_name(args.kernel, tag)}
 
     line = {
         "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(args, cfg, primary),
+        "config": {**config_dict(args, cfg, primary), "kernel": args.kernel},
         "roofline": roofline(res, "StoreF32" if primary == "fp32" else "StoreF16"),
         "gpu_launches": res["launches"],
         "clocks": clocks,

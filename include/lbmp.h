@@ -42,7 +42,8 @@ typedef int32_t lbmp_status;
 #define LBMP_ECUDA 3    /* a CUDA call failed (no device, launch error ...) */
 #define LBMP_ESTATE 4   /* call out of order (e.g. step before set_fields) */
 #define LBMP_ENAN 5     /* a reduction met a non-finite velocity or density */
-#define LBMP_ETIMEOUT 6 /* a bounded device wait gave up */
+#define LBMP_ETIMEOUT 6 /* a bounded device wait gave up (staged kernel); the
+                           state of the context is then undefined */
 
 /* boundary kinds */
 #define LBMP_BCX_PERIODIC 0
@@ -61,6 +62,12 @@ typedef int32_t lbmp_status;
 #define LBMP_ROUND_STOCHASTIC 0 /* unbiased in expectation (default) */
 #define LBMP_ROUND_NEAREST 1    /* round to nearest even */
 
+/* step kernel */
+#define LBMP_KERNEL_AUTO 0   /* the faster one measured on GB300: direct for FP32
+                                storage, staged for FP16 */
+#define LBMP_KERNEL_STAGED 1 /* bulk copies into a shared-memory ring (persistent) */
+#define LBMP_KERNEL_DIRECT 2 /* one-pass loads from global memory */
+
 #define LBMP_HOST 0
 #define LBMP_DEVICE 1
 
@@ -78,6 +85,8 @@ typedef struct lbmp_params {
   int32_t storage;      /* LBMP_STORE_* */
   int32_t fp16_log2_scale; /* s of S = 2^s for FP16 storage; 0 = automatic */
   int32_t fp16_rounding;   /* LBMP_ROUND_*: how FP16 stores round */
+  int32_t kernel;          /* LBMP_KERNEL_*: implementation of the step */
+  int32_t reserved;        /* must be 0 */
   uint64_t seed;           /* stream of the stochastic rounding (any value) */
   void *stream;         /* cudaStream_t for all work; NULL = a private stream */
 } lbmp_params;

@@ -13,6 +13,7 @@
 
 #include "kernels.h"
 #include "lattice.cuh"
+#include "staged.cuh"
 
 namespace lbmp {
 
@@ -84,6 +85,45 @@ cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const
     step_kernel<StoreF16, false><<<grid, block, 0, s>>>(a, (const __half *)fin,
                                                         (__half *)fout, med, tctr, k);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------ staged variant
+template <class S, bool SR>
+static cudaError_t launch_staged_t(const StepArgs &a, int rows, const void *fin, void *fout,
+                                   const float2 *med, const unsigned long long *tctr, int k,
+                                   unsigned *err, int nsm, cudaStream_t s) {
+  using C = StageCfg<S>;
+  using L = StageLayout<S>;
+  const int ntiles = ((a.nx + C::W - 1) / C::W) * ((rows + C::H - 1) / C::H);
+  const int grid = ntiles < nsm ? ntiles : nsm;
+  staged_step_kernel<S, SR><<<grid, kStagedThreads, L::kSmemBytes, s>>>(
+      a, (const typename S::T *)fin, (typename S::T *)fout, med, tctr, k, rows, err);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_staged() {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(staged_step_kernel<StoreF32, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           StageLayout<StoreF32>::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(staged_step_kernel<StoreF16, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           StageLayout<StoreF16>::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(staged_step_kernel<StoreF16, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              StageLayout<StoreF16>::kSmemBytes);
+}
+
+cudaError_t launch_staged(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
+                          void *fout, const float2 *med, const unsigned long long *tctr, int k,
+                          unsigned *err, int nsm, cudaStream_t s) {
+  if (rows <= 0 || a.nx <= 0) return cudaSuccess;
+  if (storage == 0)
+    return launch_staged_t<StoreF32, false>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
+  if (sr) return launch_staged_t<StoreF16, true>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
+  return launch_staged_t<StoreF16, false>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
 }
 
 cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s) {

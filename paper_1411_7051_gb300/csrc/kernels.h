@@ -35,6 +35,14 @@ __host__ __device__ inline double fc_bkc(double kn) {
 cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
                         void *fout, const float2 *med, const unsigned long long *tctr, int k,
                         cudaStream_t s);
+// Staged variant of the same step (asynchronous bulk copies into a shared-
+// memory ring, persistent grid of at most nsm CTAs); a bounded wait that
+// gives up sets *err.  prepare_staged() raises the shared-memory limit of
+// the kernels once per process.
+cudaError_t prepare_staged();
+cudaError_t launch_staged(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
+                          void *fout, const float2 *med, const unsigned long long *tctr, int k,
+                          unsigned *err, int nsm, cudaStream_t s);
 // *tctr += n (one thread).
 cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s);
 

@@ -44,6 +44,8 @@ struct StepArgs {
   int pressure;        // columns 0 and nx-1 carry imposed densities
   int forch;           // keep the Forchheimer drag of Eq. 2
   uint32_t seed_lo, seed_hi;  // stochastic rounding stream
+  int test_drop_tile;   // staged kernel: tile whose copies are withheld (-1: none);
+                        // exercises the bounded waits in tests
 };
 
 // ------------------------------------------------ hardware approximations

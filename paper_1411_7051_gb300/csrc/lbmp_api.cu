@@ -14,7 +14,7 @@
 #include <new>
 #include <string>
 
-#include "../../include/lbmp.h"
+#include "lbmp.h"
 #include "kernels.h"
 
 using lbmp::StepArgs;
@@ -81,6 +81,9 @@ struct lbmp_ctx {
   double *h_results = nullptr;  // pinned host, kNQ doubles
   unsigned *d_flag = nullptr;
   unsigned long long *d_tctr = nullptr;  // time level for the stochastic rounding
+  unsigned *d_err = nullptr;             // raised by a bounded wait that gave up
+  int nsm = 1;                           // SMs of the device
+  bool staged = true;
   bool sr = false;
   bool fields_set = false;
   int64_t steps = 0;
@@ -91,6 +94,7 @@ struct lbmp_ctx {
   int64_t device_bytes = 0;
   int alloc_count = 0;
   int fault_alloc_at = 0;       // simulated allocation failure (testing)
+  int drop_tile = -1;           // withheld tile of the staged kernel (testing)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
 
   StepArgs args() const {
@@ -117,6 +121,7 @@ struct lbmp_ctx {
     a.forch = p.forchheimer != 0;
     a.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p.seed >> 32);
+    a.test_drop_tile = drop_tile;
     return a;
   }
   int rows() const { return y_hi - y_lo; }
@@ -162,6 +167,7 @@ void release(lbmp_ctx *c) {
   cudaFree(c->results);
   cudaFree(c->d_flag);
   cudaFree(c->d_tctr);
+  cudaFree(c->d_err);
   if (c->h_results) cudaFreeHost(c->h_results);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -182,6 +188,15 @@ struct DevTemp {
   }
 };
 
+// The flag of the bounded waits (synchronous read).
+lbmp_status check_err(lbmp_ctx *c) {
+  unsigned e = 0;
+  LBMP_CK(cudaMemcpyAsync(&e, c->d_err, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+  LBMP_CK(cudaStreamSynchronize(c->stream));
+  if (e) return fail(LBMP_ETIMEOUT, "a bounded wait of the staged step kernel gave up");
+  return LBMP_OK;
+}
+
 // Run the macroscopic/reduction kernel and, when partials are requested,
 // reduce them into c->h_results (synchronous).
 lbmp_status run_macro(lbmp_ctx *c, lbmp::MacroOut o, bool reduce) {
@@ -198,18 +213,28 @@ lbmp_status run_macro(lbmp_ctx *c, lbmp::MacroOut o, bool reduce) {
                             cudaMemcpyDeviceToHost, c->stream));
   }
   LBMP_CK(cudaStreamSynchronize(c->stream));
+  lbmp_status st = check_err(c);
+  if (st) return st;
   if (reduce && c->h_results[5] != 0.0)
     return fail(LBMP_ENAN, "%.0f fluid nodes have a non-finite density or velocity",
                 c->h_results[5]);
   return LBMP_OK;
 }
 
+// One step kernel launch (the variant the context selected).
+cudaError_t launch_one(lbmp_ctx *c, const StepArgs &a, const void *fin, void *fout, int k,
+                       cudaStream_t s) {
+  if (c->staged)
+    return lbmp::launch_staged(c->p.storage, c->sr, a, c->rows(), fin, fout, c->med, c->d_tctr,
+                               k, c->d_err, c->nsm, s);
+  return lbmp::launch_step(c->p.storage, c->sr, a, c->rows(), fin, fout, c->med, c->d_tctr, k, s);
+}
+
 // n single launches (time levels *tctr + 0 .. n-1), then the counter bump.
 lbmp_status launch_steps(lbmp_ctx *c, int64_t n) {
   StepArgs a = c->args();
   for (int64_t t = 0; t < n; ++t) {
-    LBMP_CK(lbmp::launch_step(c->p.storage, c->sr, a, c->rows(), c->buf[c->cur],
-                              c->buf[c->cur ^ 1], c->med, c->d_tctr, (int)t, c->stream));
+    LBMP_CK(launch_one(c, a, c->buf[c->cur], c->buf[c->cur ^ 1], (int)t, c->stream));
     c->cur ^= 1;
     c->launches++;
   }
@@ -234,8 +259,7 @@ lbmp_status get_graph(lbmp_ctx *c, int cur, cudaGraphExec_t *out) {
   int b = cur;
   cudaError_t err = cudaSuccess;
   for (int t = 0; t < kGraphSteps && err == cudaSuccess; ++t) {
-    err = lbmp::launch_step(c->p.storage, c->sr, a, c->rows(), c->buf[b], c->buf[b ^ 1],
-                            c->med, c->d_tctr, t, c->cap_stream);
+    err = launch_one(c, a, c->buf[b], c->buf[b ^ 1], t, c->cap_stream);
     b ^= 1;
   }
   if (err == cudaSuccess && c->sr) err = lbmp::launch_bump(c->d_tctr, kGraphSteps, c->cap_stream);
@@ -297,6 +321,9 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
       return fail(LBMP_EINVAL, "storage must be LBMP_STORE_FP32 or LBMP_STORE_FP16");
     if (p.fp16_log2_scale < -60 || p.fp16_log2_scale > 60)
       return fail(LBMP_EINVAL, "fp16_log2_scale must be in [-60, 60]");
+    if (p.kernel != LBMP_KERNEL_AUTO && p.kernel != LBMP_KERNEL_STAGED && p.kernel != LBMP_KERNEL_DIRECT)
+      return fail(LBMP_EINVAL, "kernel must be LBMP_KERNEL_AUTO, _STAGED or _DIRECT");
+    if (p.reserved != 0) return fail(LBMP_EINVAL, "reserved must be 0");
     if (p.fp16_rounding != LBMP_ROUND_STOCHASTIC && p.fp16_rounding != LBMP_ROUND_NEAREST)
       return fail(LBMP_EINVAL, "fp16_rounding must be LBMP_ROUND_STOCHASTIC or LBMP_ROUND_NEAREST");
 
@@ -304,6 +331,7 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     if (!c) return fail(LBMP_ENOMEM, "host allocation of the context");
     c->p = p;
     if (const char *f = std::getenv("LBMP_FAULT_ALLOC")) c->fault_alloc_at = std::atoi(f);
+    if (const char *f = std::getenv("LBMP_TEST_DROP_TILE")) c->drop_tile = std::atoi(f);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) {
       delete c;
@@ -311,6 +339,20 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     }
     c->elem = (p.storage == LBMP_STORE_FP32) ? 4 : 2;
     c->sr = p.storage == LBMP_STORE_FP16 && p.fp16_rounding == LBMP_ROUND_STOCHASTIC;
+    // FP32: the direct kernel already saturates HBM (the staged one reaches
+    // ~0.95 of it); FP16: the staged kernel issues fewer instructions per node.
+    c->staged = p.kernel == LBMP_KERNEL_STAGED ||
+                (p.kernel == LBMP_KERNEL_AUTO && p.storage == LBMP_STORE_FP16);
+    e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "cudaDeviceGetAttribute(multiProcessorCount)");
+    }
+    e = lbmp::prepare_staged();
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "shared-memory limit of the staged kernel");
+    }
     c->pitch = ((p.nx + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
     c->plane = (long long)c->pitch * p.ny;
     c->y_lo = (p.bc_y == LBMP_BCY_WALLS) ? 1 : 0;
@@ -346,6 +388,9 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     LBMP_TRY(dalloc(c, (void **)&c->results, lbmp::kNQ * sizeof(double), "reduction results"));
     LBMP_TRY(dalloc(c, (void **)&c->d_flag, sizeof(unsigned), "validation flag"));
     LBMP_TRY(dalloc(c, (void **)&c->d_tctr, sizeof(unsigned long long), "time-level counter"));
+    LBMP_TRY(dalloc(c, (void **)&c->d_err, sizeof(unsigned), "wait error flag"));
+    e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) LBMP_TRY(cuda_fail(e, "cudaMemset"));
     e = cudaMallocHost((void **)&c->h_results, lbmp::kNQ * sizeof(double));
     if (e != cudaSuccess) LBMP_TRY(cuda_fail(e, "cudaMallocHost"));
 #undef LBMP_TRY
@@ -435,6 +480,7 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
     LBMP_CK(cudaMemsetAsync(c->buf[1], 0, c->buf_bytes(), c->stream));
     LBMP_CK(cudaMemsetAsync(c->uprev, 0, (size_t)c->plane * sizeof(float2), c->stream));
     LBMP_CK(cudaMemsetAsync(c->d_tctr, 0, sizeof(unsigned long long), c->stream));
+    LBMP_CK(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
     LBMP_CK(cudaStreamSynchronize(c->stream));
     c->cur = 0;
     c->steps = 0;
@@ -476,7 +522,7 @@ lbmp_status lbmp_synchronize(lbmp_ctx *c) {
   lbmp_status st = set_device(c);
   if (st) return st;
   LBMP_CK(cudaStreamSynchronize(c->stream));
-  return LBMP_OK;
+  return check_err(c);
 }
 
 lbmp_status lbmp_macroscopic(lbmp_ctx *c, double *rho, double *ux, double *uy,

@@ -1,0 +1,321 @@
+// Staged (asynchronous bulk-copy) variant of the porous lattice Boltzmann
+// step (Chen et al., arXiv:1411.7051, Section III, Eq. 12-17).
+//
+// The fused step moves every population once per time step, so it is
+// bound by HBM bandwidth, and bandwidth needs many bytes in flight.  Here
+// the bytes in flight do not depend on registers: a persistent CTA per SM
+// runs one producer lane that copies row tiles of the nine population
+// planes and of the medium into a ring of shared-memory stages with
+// cp.async.bulk (completion counted on an mbarrier), while sixteen consumer
+// warps pull, collide and store from the stage that has landed.
+//
+// Tile: H rows x W nodes.  A stage holds, for each plane i and tile row r,
+// the source row y - e_iy over columns [x_a - A, x_a + W + A) (A = 16 bytes
+// of halo on each side, so every copy starts and ends on a 16-byte
+// boundary), and the medium of the tile.  Sources that the stage cannot
+// hold -- the periodic wrap of column 0 / nx-1 and the bounce-back of the
+// rows next to a plate -- are read from global memory by the few threads
+// that need them.
+//
+// Every wait is bounded (kWaitNs of %globaltimer); a wait that gives up
+// raises *err and the CTA returns (the host reports LBMP_ETIMEOUT).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lattice.cuh"
+
+namespace lbmp {
+
+constexpr int kConsumerWarps = 16;
+constexpr int kStagedThreads = (kConsumerWarps + 1) * 32;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+template <class S>
+struct StageCfg;
+template <>
+struct StageCfg<StoreF32> {
+  static constexpr int W = 1024, H = 1, A = 4, STAGES = 4;
+};
+template <>
+struct StageCfg<StoreF16> {
+  static constexpr int W = 2048, H = 1, A = 8, STAGES = 4;
+};
+
+template <class S>
+struct StageLayout {
+  using C = StageCfg<S>;
+  using T = typename S::T;
+  static constexpr int RW = C::W + 2 * C::A;  // stage row length (elements)
+  static constexpr int kPopBytes = 9 * C::H * RW * (int)sizeof(T);
+  static constexpr int kMedBytes = C::H * C::W * 8;
+  static constexpr int kStageBytes = kPopBytes + kMedBytes;
+  static constexpr int kBarBytes = 128;  // full[STAGES], empty[STAGES]
+  static constexpr int kSmemBytes = kBarBytes + C::STAGES * kStageBytes;
+  static_assert(kPopBytes % 16 == 0 && kStageBytes % 16 == 0, "16-byte stage alignment");
+  static_assert(RW * (int)sizeof(T) % 16 == 0, "16-byte row alignment");
+  static_assert(C::A * (int)sizeof(T) == 16, "halo of 16 bytes");
+  static_assert(2 * C::STAGES * 8 <= kBarBytes, "barrier area");
+  static_assert((C::H * C::W) % (kConsumerWarps * 32) == 0, "nodes per consumer thread");
+};
+
+// ------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase of parity `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned *err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 30); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) break;
+  }
+  atomicOr(err, 1u);
+  return false;
+}
+// Global -> shared bulk copy; completion is counted on mbarrier `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// --------------------------------------------------------------- helpers
+// Source row of plane i for target row y: y - e_iy (periodic wrap), or -1
+// when it is a plate row (the target then bounces back).
+__device__ __forceinline__ int staged_src_row(const StepArgs &a, int i, int y) {
+  const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+  int ys = y - ey;
+  if (a.walls && (ys == 0 || ys == a.ny - 1) && ey != 0) return -1;
+  if (ys < 0) ys += a.ny;
+  if (ys >= a.ny) ys -= a.ny;
+  return ys;
+}
+
+// Post-stream values of node (x, y) at tile position (r, c), stored units.
+template <class S>
+__device__ __forceinline__ void pull_staged(const typename S::T *__restrict__ sp,
+                                            const typename S::T *__restrict__ fin,
+                                            const StepArgs &a, int r, int c, int x, int y,
+                                            float d[9]) {
+  using L = StageLayout<S>;
+  using C = StageCfg<S>;
+  constexpr int RW = L::RW, A = C::A, H = C::H;
+  const typename S::T *row[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) row[i] = sp + (i * H + r) * RW + A + c;
+  // columns with e_x = 0 and the shifted ones
+  d[0] = S::ld1(row[0]);
+  d[2] = S::ld1(row[2]);
+  d[4] = S::ld1(row[4]);
+  d[1] = S::ld1(row[1] - 1);
+  d[5] = S::ld1(row[5] - 1);
+  d[8] = S::ld1(row[8] - 1);
+  d[3] = S::ld1(row[3] + 1);
+  d[6] = S::ld1(row[6] + 1);
+  d[7] = S::ld1(row[7] + 1);
+  const bool xlo = !a.pressure && x == 0;           // e_x = +1 sources wrap to nx-1
+  const bool xhi = !a.pressure && x == a.nx - 1;    // e_x = -1 sources wrap to 0
+  const bool wm = a.walls && y == 1;                // e_y = +1 sources are a plate
+  const bool wp = a.walls && y == a.ny - 2;         // e_y = -1 sources are a plate
+  if (xlo || xhi || wm || wp) {
+    const long long P = a.plane;
+    const int ym = (y == 0) ? a.ny - 1 : y - 1;
+    const int yp = (y == a.ny - 1) ? 0 : y + 1;
+    const long long rr = (long long)y * a.pitch, rm = (long long)ym * a.pitch,
+                    rp = (long long)yp * a.pitch;
+    if (xlo) {
+      const int xs = a.nx - 1;
+      d[1] = S::ld1(fin + 1 * P + rr + xs);
+      d[5] = S::ld1(fin + 5 * P + rm + xs);
+      d[8] = S::ld1(fin + 8 * P + rp + xs);
+    }
+    if (xhi) {
+      d[3] = S::ld1(fin + 3 * P + rr);
+      d[6] = S::ld1(fin + 6 * P + rm);
+      d[7] = S::ld1(fin + 7 * P + rp);
+    }
+    if (wm) {
+      d[2] = S::ld1(fin + 4 * P + rr + x);
+      d[5] = S::ld1(fin + 7 * P + rr + x);
+      d[6] = S::ld1(fin + 8 * P + rr + x);
+    }
+    if (wp) {
+      d[4] = S::ld1(fin + 2 * P + rr + x);
+      d[7] = S::ld1(fin + 5 * P + rr + x);
+      d[8] = S::ld1(fin + 6 * P + rr + x);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ kernel
+template <class S, bool SR>
+__global__ void __launch_bounds__(kStagedThreads, 1)
+    staged_step_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
+                       typename S::T *__restrict__ fout, const float2 *__restrict__ med,
+                       const unsigned long long *__restrict__ tctr, int k, int rows,
+                       unsigned *err) {
+  using L = StageLayout<S>;
+  using C = StageCfg<S>;
+  using T = typename S::T;
+  constexpr int W = C::W, H = C::H, A = C::A, NS = C::STAGES, RW = L::RW;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t sbase = smem_u32(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto full = [&](int s) { return sbase + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return sbase + 8u * (uint32_t)(NS + s); };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int tiles_x = (a.nx + W - 1) / W;
+  const int tiles_y = (rows + H - 1) / H;
+  const int ntiles = tiles_x * tiles_y;
+  const int y_end = a.y0 + rows;
+
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------- producer
+    // The copies of a tile (9 planes x H rows, then H medium rows) are
+    // spread over the lanes of this warp, which issue them concurrently
+    // after lane 0 has posted the expected byte count.
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int s = it % NS;
+      const uint32_t use = (uint32_t)(it / NS);
+      if (use > 0) {
+        if (lane == 0) ok = mbar_wait(empty(s), (use - 1) & 1u, err);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
+      if (!ok) {
+        // consumers are gone: let the copies already issued land, then leave
+        if (lane == 0)
+          for (int j = 1; j < NS && j <= it; ++j)
+            mbar_wait(full((it - j) % NS), (uint32_t)((it - j) / NS) & 1u, err);
+        return;
+      }
+      const int ya = a.y0 + (t / tiles_x) * H;
+      const int xa = (t % tiles_x) * W;
+      const int nrow = min(H, y_end - ya);
+      const int gx0 = max(xa - A, 0), gx1 = min(xa + W + A, a.pitch);
+      const uint32_t row_bytes = (uint32_t)(gx1 - gx0) * (uint32_t)sizeof(T);
+      const int scol = gx0 - (xa - A);
+      const uint32_t med_bytes = (uint32_t)(min(xa + W, a.pitch) - xa) * 8u;
+      const int ncopy = 10 * nrow;  // copy j < 9 nrow: plane j / nrow, row j % nrow
+      if (lane == 0) {
+        uint32_t total = (uint32_t)nrow * med_bytes;
+        for (int i = 0; i < 9; ++i)
+          for (int r = 0; r < nrow; ++r)
+            if (staged_src_row(a, i, ya + r) >= 0) total += row_bytes;
+        mbar_arrive_expect_tx(full(s), total);
+      }
+      __syncwarp();
+      if (t == a.test_drop_tile) continue;  // the consumers' wait must run out
+      const uint32_t st = sbase + (uint32_t)L::kBarBytes + (uint32_t)s * (uint32_t)L::kStageBytes;
+      for (int j = lane; j < ncopy; j += 32) {
+        if (j < 9 * nrow) {
+          const int i = j / nrow, r = j % nrow;
+          const int ys = staged_src_row(a, i, ya + r);
+          if (ys < 0) continue;
+          const uint32_t dst = st + (uint32_t)(((i * H + r) * RW + scol) * (int)sizeof(T));
+          const T *src = fin + (long long)i * a.plane + (long long)ys * a.pitch + gx0;
+          bulk_g2s(dst, src, row_bytes, full(s));
+        } else {
+          const int r = j - 9 * nrow;
+          const uint32_t dst = st + (uint32_t)L::kPopBytes + (uint32_t)(r * W * 8);
+          bulk_g2s(dst, med + (long long)(ya + r) * a.pitch + xa, med_bytes, full(s));
+        }
+      }
+    }
+    return;
+  }
+
+  // --------------------------------------------------------- consumers
+  uint32_t ts = 0;
+  if (SR) {
+    const unsigned long long tl = *tctr + (unsigned long long)k;
+    ts = mix32((uint32_t)tl * 0x9e3779b9u ^ a.seed_lo ^ mix32((uint32_t)(tl >> 32) ^ a.seed_hi));
+  }
+  constexpr int kPer = (H * W) / (kConsumerWarps * 32);
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int s = it % NS;
+    if (!mbar_wait(full(s), (uint32_t)(it / NS) & 1u, err)) return;
+    const int ya = a.y0 + (t / tiles_x) * H;
+    const int xa = (t % tiles_x) * W;
+    const int nrow = min(H, y_end - ya);
+    const unsigned char *sb = smem + L::kBarBytes + s * L::kStageBytes;
+    const T *sp = reinterpret_cast<const T *>(sb);
+    const float2 *sm = reinterpret_cast<const float2 *>(sb + L::kPopBytes);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int q = threadIdx.x + j * kConsumerWarps * 32;
+      const int r = q / W, c = q % W;
+      const int x = xa + c, y = ya + r;
+      if (r >= nrow || x >= a.nx) continue;
+      float d[9];
+      pull_staged<S>(sp, fin, a, r, c, x, y, d);
+      const float2 m = sm[r * W + c];
+      if (a.pressure && (x == 0 || x == a.nx - 1)) {
+        // non-equilibrium extrapolation from the adjacent interior node
+        const int cn = (x == 0) ? c + 1 : c - 1;
+        const int xn = (x == 0) ? 1 : a.nx - 2;
+        const float2 mn = med[(long long)y * a.pitch + xn];
+        float dn[9];
+        pull_staged<S>(sp, fin, a, r, cn, xn, y, dn);
+        const NodeState sn = node_state(dn, mn.x, mn.y, a);
+        const float drho_b = (x == 0) ? a.drho_in : a.drho_out;
+        float eq_b[9], eq_n[9];
+        equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, m.x, eq_b);
+        equilibrium_dev(sn.drho_s * a.inv_scale, sn.rho, sn.ux, sn.uy, mn.x, eq_n);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = fmaf(a.scale, eq_b[i] - eq_n[i], dn[i]);
+      }
+      const NodeState ns = node_state(d, m.x, m.y, a);
+      collide(d, ns, a);
+      const long long o = (long long)y * a.pitch + x;
+      const uint32_t h = SR ? mix32((uint32_t)o ^ ts) : 0u;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) S::template st1r<SR>(fout + i * a.plane + o, d[i], h, i);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty(s));
+  }
+}
+
+}  // namespace lbmp

@@ -24,6 +24,7 @@ BCX_PERIODIC, BCX_PRESSURE = 0, 1
 BCY_PERIODIC, BCY_WALLS = 0, 1
 STORE_FP32, STORE_FP16 = 0, 1
 ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
+KERNEL_AUTO, KERNEL_STAGED, KERNEL_DIRECT = 0, 1, 2
 HOST, DEVICE = 0, 1
 
 _STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE",
@@ -46,6 +47,7 @@ class Params(ctypes.Structure):
         ("rho0", ctypes.c_double), ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
         ("forchheimer", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("fp16_log2_scale", ctypes.c_int32), ("fp16_rounding", ctypes.c_int32),
+        ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
     ]
 
@@ -151,6 +153,7 @@ class SimConfig:
     storage: int = STORE_FP32
     fp16_log2_scale: int = 0
     fp16_rounding: int = ROUND_STOCHASTIC
+    kernel: int = KERNEL_AUTO
     seed: int = 0
 
     def to_params(self, stream: int | None) -> Params:
@@ -158,7 +161,8 @@ class SimConfig:
                       float(self.G[0]), float(self.G[1]), int(self.bc_x), int(self.bc_y),
                       float(self.rho0), float(self.rho_in), float(self.rho_out),
                       int(self.forchheimer), int(self.storage), int(self.fp16_log2_scale),
-                      int(self.fp16_rounding), int(self.seed) & (2**64 - 1), stream)
+                      int(self.fp16_rounding), int(self.kernel), 0,
+                      int(self.seed) & (2**64 - 1), stream)
 
 
 class Sim:

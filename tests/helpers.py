@@ -37,7 +37,7 @@ def oracle_sim(orc, case: Case):
 
 
 def gpu_sim(case: Case, storage: int = 0, fp16_log2_scale: int = 0, fp16_rounding: int = 0,
-            seed: int = 0):
+            seed: int = 0, kernel: int = 0):
     from paper_1411_7051_gb300 import lbmp
     cfg = lbmp.SimConfig(case.nx, case.ny, tau=case.tau, G=case.G,
                          bc_x=lbmp.BCX_PRESSURE if case.pressure else lbmp.BCX_PERIODIC,
@@ -45,7 +45,7 @@ def gpu_sim(case: Case, storage: int = 0, fp16_log2_scale: int = 0, fp16_roundin
                          rho_in=case.rho_in, rho_out=case.rho_out,
                          forchheimer=case.forchheimer, storage=storage,
                          fp16_log2_scale=fp16_log2_scale, fp16_rounding=fp16_rounding,
-                         seed=seed)
+                         seed=seed, kernel=kernel)
     s = lbmp.Sim(cfg)
     m = case.medium
     s.set_fields(m.eps, m.k_i, m.kn)

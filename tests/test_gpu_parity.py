@@ -31,6 +31,7 @@ pytestmark = pytest.mark.gpu
 
 FP32, FP16 = 0, 1
 SR, RN = 0, 1
+STAGED, DIRECT = 1, 2
 
 
 def _np(t):
@@ -70,9 +71,10 @@ ONE_STEP_CASES = {
 }
 
 
+@pytest.mark.parametrize("kernel", [STAGED, DIRECT])
 @pytest.mark.parametrize("name", list(ONE_STEP_CASES))
-@pytest.mark.parametrize("nx,ny", [(131, 37), (300, 9), (1, 5), (5, 1)])
-def test_one_step_from_random_state(orc, name, nx, ny):
+@pytest.mark.parametrize("nx,ny", [(131, 37), (300, 9), (1, 5), (5, 1), (257, 6)])
+def test_one_step_from_random_state(orc, name, nx, ny, kernel):
     kw = ONE_STEP_CASES[name]
     if kw["walls"] and ny < 3 or kw["pressure"] and nx < 3:
         pytest.skip("lattice too small for this boundary kind")
@@ -84,7 +86,7 @@ def test_one_step_from_random_state(orc, name, nx, ny):
     f0 = media.random_populations(nx, ny, seed=3, base=w, amp=2e-3)
     osim = oracle_sim(orc, case)
     osim.set_populations(f0)
-    gs = gpu_sim(case, FP32)
+    gs = gpu_sim(case, FP32, kernel=kernel)
     gs.set_populations(f0)
     fr = fluid_rows(case)
     # the loaded state itself (pressure columns re-extrapolated on both sides)
@@ -290,6 +292,38 @@ def test_checkpoint_restart_bitwise(storage):
     assert b.info().steps == 50
     b.step(50)
     assert np.array_equal(_np(a.populations()), _np(b.populations()))
+
+
+@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("walls,pressure", [(True, True), (False, False), (True, False)])
+def test_staged_matches_direct(storage, walls, pressure):
+    med = media.random_medium(300, 41, seed=12, p_open=0.1, p_solid=0.1, log10_k_range=(-3, 0))
+    case = Case(300, 41, tau=0.7, G=(1e-5, 0.0), walls=walls, pressure=pressure,
+                rho_in=1.001, rho_out=0.999, forchheimer=1, medium=med)
+    a = gpu_sim(case, storage, kernel=STAGED)
+    b = gpu_sim(case, storage, kernel=DIRECT)
+    a.step(50)
+    b.step(50)
+    fa, fb = _np(a.populations()), _np(b.populations())
+    np.testing.assert_allclose(fa, fb, rtol=0, atol=1e-12)
+
+
+def test_bounded_wait_reports_timeout(monkeypatch):
+    """The staged kernel's waits are bounded: with the copies of one tile
+    withheld, the consumers give up after their limit, the host reports
+    ETIMEOUT, and the context stays usable."""
+    from paper_1411_7051_gb300 import lbmp
+    monkeypatch.setenv("LBMP_TEST_DROP_TILE", "3")
+    case = _two_component_case(n=1024, ny=64)
+    gs = gpu_sim(case, FP32, kernel=STAGED)
+    monkeypatch.delenv("LBMP_TEST_DROP_TILE")
+    gs.step(1)
+    with pytest.raises(lbmp.LbmpError) as ei:
+        gs.synchronize()
+    assert ei.value.status == lbmp.ETIMEOUT
+    ok = gpu_sim(case, FP32, kernel=STAGED)   # a fresh context works
+    ok.step(5)
+    ok.synchronize()
 
 
 def test_stochastic_rounding_is_seeded():
