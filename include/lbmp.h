@@ -183,6 +183,35 @@ lbmp_status lbmp_set_state(lbmp_ctx *ctx, const void *buf, size_t bytes, int32_t
 /* Sizes, storage and counters of ctx. */
 lbmp_status lbmp_get_info(lbmp_ctx *ctx, lbmp_info *out);
 
+/* Global permeability of a lattice state held entirely in caller memory,
+ * allocating nothing.  The paper has no counterpart: this serves callers
+ * that cannot call cudaMalloc -- code that runs while another component
+ * holds the device in a stream capture, processes whose device memory is
+ * owned by another framework's pool, latency-bound loops that may not pay
+ * for an allocation.  It computes what lbmp_permeability computes (Darcy's
+ * law over the whole domain with eps p = c_s^2 rho for the pressure drop),
+ * in FP64, from:
+ *   p            lattice size, tau, J, G, boundary kinds, rho0, rho_in,
+ *                rho_out, forchheimer (other fields ignored);
+ *   f            device, [9][ny][nx] float64 post-stream populations, as
+ *                lbmp_populations(..., LBMP_DEVICE) returns them;
+ *   eps,k_i,kn   device, [ny][nx] float64 medium as for lbmp_set_fields;
+ *   out          device, 3 doubles: k_g, <u_x>, number of fluid nodes whose
+ *                velocity is not finite;
+ *   stream       cudaStream_t (NULL: the legacy default stream); the call
+ *                is asynchronous on it.
+ * Scratch: the per-block partial sums live in a fixed 2 MiB array inside
+ * the library (held by every GPU that loads it until exit), so the lattice
+ * may need at most 65536 reduction blocks: ceil(nx / 256) * ny <= 65536
+ * (e.g. 4096 x 4096); larger lattices get LBMP_EINVAL.  Every call uses the
+ * same array: calls that overlap on the GPU (other streams, other threads)
+ * race.  The first call on each device looks up the array's device address
+ * (once, under a lock); make that first call before any stream capture.
+ * Errors: EINVAL (NULL pointer, bad size), ECUDA. */
+lbmp_status lbmp_permeability_noalloc(const lbmp_params *p, const double *f, const double *eps,
+                                      const double *k_i, const double *kn, double *out,
+                                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,9 @@ cudaError_t prepare_staged();
 cudaError_t launch_staged(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
                           void *fout, const float2 *med, const unsigned long long *tctr, int k,
                           unsigned *err, int nsm, cudaStream_t s);
+// Store msg as the calling thread's lbmp_last_error() text.
+void set_last_error(const char *msg);
+
 // *tctr += n (one thread).
 cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s);
 

@@ -20,8 +20,12 @@
 using lbmp::StepArgs;
 
 namespace {
-
 thread_local std::string g_err;
+}
+
+void lbmp::set_last_error(const char *msg) { g_err = msg; }
+
+namespace {
 
 lbmp_status fail(lbmp_status st, const char *fmt, ...) {
   char buf[512];

@@ -118,6 +118,8 @@ def load(path: str = LIB_PATH):
     L.lbmp_set_state.argtypes = [_VP, _VP, ctypes.c_size_t, ctypes.c_int32]
     L.lbmp_get_info.restype = st
     L.lbmp_get_info.argtypes = [_VP, ctypes.POINTER(Info)]
+    L.lbmp_permeability_noalloc.restype = st
+    L.lbmp_permeability_noalloc.argtypes = [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]
     _lib = L
     return L
 
@@ -130,6 +132,26 @@ def _check(status: int):
 def fc(kn: float) -> float:
     """Eq. 6-7 correction factor, evaluated by the library (host code)."""
     return float(load().lbmp_fc(float(kn)))
+
+
+def permeability_noalloc(cfg: "SimConfig", f, eps, k_i, kn, out, stream=None):
+    """``lbmp_permeability_noalloc``: k_g, <u_x> and the non-finite count of
+    a state held in caller device memory, written to ``out`` (3 float64 on
+    the device), asynchronously on ``stream`` (a torch.cuda.Stream; default:
+    the current stream).  All tensors: contiguous float64 CUDA tensors, f of
+    shape [9, ny, nx], the medium [ny, nx]."""
+    torch = _torch()
+    for t in (f, eps, k_i, kn, out):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous()):
+            raise TypeError("permeability_noalloc takes contiguous float64 CUDA tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    params = cfg.to_params(None)
+    _check(load().lbmp_permeability_noalloc(
+        ctypes.byref(params), ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(eps.data_ptr()),
+        ctypes.c_void_p(k_i.data_ptr()), ctypes.c_void_p(kn.data_ptr()),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream)))
 
 
 def _torch():
