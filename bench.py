@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--fp16-rounding", choices=["stochastic", "nearest"], default="stochastic")
     ap.add_argument("--kernel", choices=["auto", "staged", "direct"], default="auto",
                     help="implementation of the step kernel (auto: direct for FP32 storage, "
                          "staged for FP16)")
@@ -220,13 +221,15 @@ def config_dict(args, cfg, storage):
 
 
 # ------------------------------------------------------------- GPU (ours)
-def time_storage(lbmp, torch, med, cfg, storage, K, W, kernel):
+def time_storage(lbmp, torch, med, cfg, storage, K, W, kernel, rounding="stochastic"):
     st = lbmp.STORE_FP32 if storage == "fp32" else lbmp.STORE_FP16
     sc = lbmp.SimConfig(cfg["nx"], cfg["ny"], tau=cfg["tau"], bc_x=cfg["bc_x"],
                         bc_y=cfg["bc_y"], rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
                         forchheimer=cfg["forchheimer"], storage=st,
                         kernel={"auto": lbmp.KERNEL_AUTO, "staged": lbmp.KERNEL_STAGED,
-                                "direct": lbmp.KERNEL_DIRECT}[kernel])
+                                "direct": lbmp.KERNEL_DIRECT}[kernel],
+                        fp16_rounding=(lbmp.ROUND_STOCHASTIC if rounding == "stochastic"
+                                       else lbmp.ROUND_NEAREST))
     sim = lbmp.Sim(sc)
     sim.set_fields(med.eps, med.k_i, med.kn)
     sim.step(W)
@@ -294,11 +297,12 @@ def run_ours(args, ws, rank, local):
     other = "fp16" if primary == "fp32" else "fp32"
 
     with ClockSampler(local) as clk:
-        res = time_storage(lbmp, torch, med, cfg, primary, K, W, args.kernel)
+        res = time_storage(lbmp, torch, med, cfg, primary, K, W, args.kernel, args.fp16_rounding)
     clocks = clk.summary()
     res_other = None
     if not args.no_other:
-        res_other = time_storage(lbmp, torch, med, cfg, other, K, W, args.kernel)
+        res_other = time_storage(lbmp, torch, med, cfg, other, K, W, args.kernel,
+                                 args.fp16_rounding)
     e2e = None if args.no_e2e else time_e2e(lbmp, torch, med, cfg, K)
 
     # slowest rank decides
@@ -337,7 +341,8 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**config_dict(args, cfg, primary), "kernel": args.kernel},
+        "config": {**config_dict(args, cfg, primary), "kernel": args.kernel,
+                   "fp16_rounding": args.fp16_rounding},
         "roofline": roofline(res, "StoreF32" if primary == "fp32" else "StoreF16"),
         "gpu_launches": res["launches"],
         "clocks": clocks,

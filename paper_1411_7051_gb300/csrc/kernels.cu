@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kStepBX)
     if (x >= a.nx) continue;
     if (a.pressure && (x == 0 || x == a.nx - 1)) pressure_node<S>(fin, med, a, x, y, m[j].x, d[j]);
     const NodeState s = node_state(d[j], m[j].x, m[j].y, a);
-    collide(d[j], s, a);
+    collide<S::kHiLo>(d[j], s, a);
     typename S::T *o = fout + row + x;
     const uint32_t h = SR ? mix32((uint32_t)(row + x) ^ ts) : 0u;
 #pragma unroll

@@ -86,6 +86,7 @@ struct StoreF32 {
   static __device__ __forceinline__ void st1(float *p, float v) { *p = v; }
   template <bool SR>
   static __device__ __forceinline__ void st1r(float *p, float v, uint32_t, int) { *p = v; }
+  static constexpr bool kHiLo = true;
   template <bool SR>
   static __device__ __forceinline__ void st2(float *p, float a, float b, uint32_t, uint32_t) {
     *reinterpret_cast<float2 *>(p) = make_float2(a, b);
@@ -101,6 +102,7 @@ struct StoreF16 {
     b = v.y;
   }
   static __device__ __forceinline__ void st1(__half *p, float v) { *p = __float2half_rn(v); }
+  static constexpr bool kHiLo = false;
   // Scalar store; with SR the 8 random bits of direction i come from the
   // node hash h times an odd constant of that direction.
   template <bool SR>
@@ -118,18 +120,17 @@ struct StoreF16 {
       *p = __float2half_rn(v);
     }
   }
-  // SR: add a random 13-bit offset below the FP16 mantissa to the FP32 bit
-  // pattern, then truncate toward zero; a value between two FP16 neighbours
-  // rounds up with probability equal to its distance from the lower one
-  // (exact for FP16 normals).  Otherwise round to nearest even.
+  // Node pair -> one 32-bit word.  SR: the hardware stochastic rounding
+  // cvt.rs, whose random operand supplies bits 31..16 to the upper half
+  // (node b) and bits 15..0 to the lower half (node a); a value between two
+  // FP16 neighbours rounds up with probability equal to its distance from
+  // the lower one.  Otherwise round to nearest even.
   template <bool SR>
-  static __device__ __forceinline__ void st2(__half *p, float a, float b, uint32_t ra,
-                                             uint32_t rb) {
+  static __device__ __forceinline__ void st2(__half *p, float a, float b, uint32_t rbits,
+                                             uint32_t) {
     uint32_t packed;
     if (SR) {
-      const float sa = __uint_as_float(__float_as_uint(a) + ra);
-      const float sb = __uint_as_float(__float_as_uint(b) + rb);
-      asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(packed) : "f"(sb), "f"(sa));
+      asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(packed) : "f"(b), "f"(a), "r"(rbits));
     } else {
       const __half2 h = __floats2half2_rn(a, b);
       packed = *reinterpret_cast<const uint32_t *>(&h);
@@ -240,8 +241,14 @@ constexpr float kW0l = (float)(4.0 / 9.0 - (double)kW0h);
 constexpr float kW1l = (float)(1.0 / 9.0 - (double)kW1h);
 constexpr float kW2l = (float)(1.0 / 36.0 - (double)kW2h);
 
-__device__ __forceinline__ float wmul(float wh, float wl, float t) { return fmaf(wh, t, wl * t); }
+template <bool HILO>
+__device__ __forceinline__ float wmul(float wh, float wl, float t) {
+  return HILO ? fmaf(wh, t, wl * t) : wh * t;
+}
 
+// HILO = false drops the lo parts of the weights: for FP16 storage the FP16
+// rounding (zero-mean with stochastic rounding) dominates their effect.
+template <bool HILO = true>
 __device__ __forceinline__ void collide(float d[9], const NodeState &s, const StepArgs &a) {
   const float mx = s.mx, my = s.my;
   const float rs = s.rho * a.scale;
@@ -261,15 +268,15 @@ __device__ __forceinline__ void collide(float d[9], const NodeState &s, const St
   const float s5 = sd + Mxy2, s6 = sd - Mxy2;
   const float pp = Px + Py, pm = Px - Py;
   const float o1 = a.one_m_omega;
-  d[0] = fmaf(o1, d[0], wmul(kW0h, kW0l, A));
-  d[1] = fmaf(o1, d[1], wmul(kW1h, kW1l, sx + Px));
-  d[3] = fmaf(o1, d[3], wmul(kW1h, kW1l, sx - Px));
-  d[2] = fmaf(o1, d[2], wmul(kW1h, kW1l, sy + Py));
-  d[4] = fmaf(o1, d[4], wmul(kW1h, kW1l, sy - Py));
-  d[5] = fmaf(o1, d[5], wmul(kW2h, kW2l, s5 + pp));
-  d[7] = fmaf(o1, d[7], wmul(kW2h, kW2l, s5 - pp));
-  d[6] = fmaf(o1, d[6], wmul(kW2h, kW2l, s6 - pm));
-  d[8] = fmaf(o1, d[8], wmul(kW2h, kW2l, s6 + pm));
+  d[0] = fmaf(o1, d[0], wmul<HILO>(kW0h, kW0l, A));
+  d[1] = fmaf(o1, d[1], wmul<HILO>(kW1h, kW1l, sx + Px));
+  d[3] = fmaf(o1, d[3], wmul<HILO>(kW1h, kW1l, sx - Px));
+  d[2] = fmaf(o1, d[2], wmul<HILO>(kW1h, kW1l, sy + Py));
+  d[4] = fmaf(o1, d[4], wmul<HILO>(kW1h, kW1l, sy - Py));
+  d[5] = fmaf(o1, d[5], wmul<HILO>(kW2h, kW2l, s5 + pp));
+  d[7] = fmaf(o1, d[7], wmul<HILO>(kW2h, kW2l, s5 - pp));
+  d[6] = fmaf(o1, d[6], wmul<HILO>(kW2h, kW2l, s6 - pm));
+  d[8] = fmaf(o1, d[8], wmul<HILO>(kW2h, kW2l, s6 + pm));
 }
 
 // Deviation of the porous equilibrium (Eq. 14) from w_i rho0, physical

@@ -6,7 +6,7 @@
 // the bytes in flight do not depend on registers: a persistent CTA per SM
 // runs one producer lane that copies row tiles of the nine population
 // planes and of the medium into a ring of shared-memory stages with
-// cp.async.bulk (completion counted on an mbarrier), while sixteen consumer
+// cp.async.bulk (completion counted on an mbarrier), while 24 consumer
 // warps pull, collide and store from the stage that has landed.
 //
 // Tile: H rows x W nodes.  A stage holds, for each plane i and tile row r,
@@ -28,7 +28,7 @@
 
 namespace lbmp {
 
-constexpr int kConsumerWarps = 16;
+constexpr int kConsumerWarps = 24;
 constexpr int kStagedThreads = (kConsumerWarps + 1) * 32;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
@@ -36,11 +36,11 @@ template <class S>
 struct StageCfg;
 template <>
 struct StageCfg<StoreF32> {
-  static constexpr int W = 1024, H = 1, A = 4, STAGES = 4;
+  static constexpr int W = 1536, H = 1, A = 4, STAGES = 3;
 };
 template <>
 struct StageCfg<StoreF16> {
-  static constexpr int W = 2048, H = 1, A = 8, STAGES = 4;
+  static constexpr int W = 1536, H = 1, A = 8, STAGES = 5;
 };
 
 template <class S>
@@ -57,7 +57,8 @@ struct StageLayout {
   static_assert(RW * (int)sizeof(T) % 16 == 0, "16-byte row alignment");
   static_assert(C::A * (int)sizeof(T) == 16, "halo of 16 bytes");
   static_assert(2 * C::STAGES * 8 <= kBarBytes, "barrier area");
-  static_assert((C::H * C::W) % (kConsumerWarps * 32) == 0, "nodes per consumer thread");
+  static_assert((C::H * C::W / 2) % (kConsumerWarps * 32) == 0, "node pairs per consumer thread");
+  static_assert(C::W % 2 == 0 && C::A % 2 == 0, "pairs stay aligned");
 };
 
 // ------------------------------------------------------------- PTX helpers
@@ -271,7 +272,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const unsigned long long tl = *tctr + (unsigned long long)k;
     ts = mix32((uint32_t)tl * 0x9e3779b9u ^ a.seed_lo ^ mix32((uint32_t)(tl >> 32) ^ a.seed_hi));
   }
-  constexpr int kPer = (H * W) / (kConsumerWarps * 32);
+  // Each consumer thread owns node pairs (x0, x0 + 1), x0 even, of the tile.
+  constexpr int kPairs = (H * W / 2) / (kConsumerWarps * 32);
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
     const int s = it % NS;
@@ -282,36 +284,71 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const unsigned char *sb = smem + L::kBarBytes + s * L::kStageBytes;
     const T *sp = reinterpret_cast<const T *>(sb);
     const float2 *sm = reinterpret_cast<const float2 *>(sb + L::kPopBytes);
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int q = threadIdx.x + j * kConsumerWarps * 32;
-      const int r = q / W, c = q % W;
+#pragma unroll 1
+    for (int j = 0; j < kPairs; ++j) {
+      const int q = threadIdx.x + j * kConsumerWarps * 32;  // pair index in the tile
+      const int r = (2 * q) / W, c = (2 * q) % W;
       const int x = xa + c, y = ya + r;
       if (r >= nrow || x >= a.nx) continue;
-      float d[9];
-      pull_staged<S>(sp, fin, a, r, c, x, y, d);
-      const float2 m = sm[r * W + c];
-      if (a.pressure && (x == 0 || x == a.nx - 1)) {
-        // non-equilibrium extrapolation from the adjacent interior node
-        const int cn = (x == 0) ? c + 1 : c - 1;
-        const int xn = (x == 0) ? 1 : a.nx - 2;
-        const float2 mn = med[(long long)y * a.pitch + xn];
-        float dn[9];
-        pull_staged<S>(sp, fin, a, r, cn, xn, y, dn);
-        const NodeState sn = node_state(dn, mn.x, mn.y, a);
-        const float drho_b = (x == 0) ? a.drho_in : a.drho_out;
-        float eq_b[9], eq_n[9];
-        equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, m.x, eq_b);
-        equilibrium_dev(sn.drho_s * a.inv_scale, sn.rho, sn.ux, sn.uy, mn.x, eq_n);
+      const bool two = x + 1 < a.nx;
+      float dA[9], dB[9];
+      const float4 m = *reinterpret_cast<const float4 *>(sm + r * W + c);
+      const bool edge = x == 0 || x + 2 >= a.nx || (a.walls && (y == 1 || y == a.ny - 2));
+      if (!edge) {
+        // interior pair: e_x = 0 directions as one vector read per plane
+        const T *row = sp + r * RW + A + c;
+        constexpr int PL = H * RW;  // elements between planes in a stage
+        S::ld2(row, dA[0], dB[0]);
+        S::ld2(row + 2 * PL, dA[2], dB[2]);
+        S::ld2(row + 4 * PL, dA[4], dB[4]);
+        dA[1] = S::ld1(row + 1 * PL - 1); dB[1] = S::ld1(row + 1 * PL);
+        dA[5] = S::ld1(row + 5 * PL - 1); dB[5] = S::ld1(row + 5 * PL);
+        dA[8] = S::ld1(row + 8 * PL - 1); dB[8] = S::ld1(row + 8 * PL);
+        dA[3] = S::ld1(row + 3 * PL + 1); dB[3] = S::ld1(row + 3 * PL + 2);
+        dA[6] = S::ld1(row + 6 * PL + 1); dB[6] = S::ld1(row + 6 * PL + 2);
+        dA[7] = S::ld1(row + 7 * PL + 1); dB[7] = S::ld1(row + 7 * PL + 2);
+      } else {
+        pull_staged<S>(sp, fin, a, r, c, x, y, dA);
+        if (two) pull_staged<S>(sp, fin, a, r, c + 1, x + 1, y, dB);
+        if (a.pressure) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] = fmaf(a.scale, eq_b[i] - eq_n[i], dn[i]);
+          for (int h = 0; h < 2; ++h) {
+            const int xb = x + h;
+            if (!(xb == 0 || xb == a.nx - 1) || (h == 1 && !two)) continue;
+            float *d = h ? dB : dA;
+            const int cn = (xb == 0) ? c + h + 1 : c + h - 1;
+            const int xn = (xb == 0) ? 1 : a.nx - 2;
+            const float2 mn = med[(long long)y * a.pitch + xn];
+            float dn[9];
+            pull_staged<S>(sp, fin, a, r, cn, xn, y, dn);
+            const NodeState sn = node_state(dn, mn.x, mn.y, a);
+            const float drho_b = (xb == 0) ? a.drho_in : a.drho_out;
+            float eq_b[9], eq_n[9];
+            equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, h ? m.z : m.x, eq_b);
+            equilibrium_dev(sn.drho_s * a.inv_scale, sn.rho, sn.ux, sn.uy, mn.x, eq_n);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i] = fmaf(a.scale, eq_b[i] - eq_n[i], dn[i]);
+          }
+        }
       }
-      const NodeState ns = node_state(d, m.x, m.y, a);
-      collide(d, ns, a);
+      const NodeState nA = node_state(dA, m.x, m.y, a);
+      collide<S::kHiLo>(dA, nA, a);
       const long long o = (long long)y * a.pitch + x;
-      const uint32_t h = SR ? mix32((uint32_t)o ^ ts) : 0u;
+      if (two) {
+        const NodeState nB = node_state(dB, m.z, m.w, a);
+        collide<S::kHiLo>(dB, nB, a);
+        const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
+        constexpr uint32_t kC[9] = {0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du, 0x27d4eb2fu,
+                                    0x165667b1u, 0xd3a2646du, 0xfd7046c5u, 0xb55a4f09u,
+                                    0x7feb352du};
 #pragma unroll
-      for (int i = 0; i < 9; ++i) S::template st1r<SR>(fout + i * a.plane + o, d[i], h, i);
+        for (int i = 0; i < 9; ++i)  // 32 random bits per direction and pair
+          S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? h * kC[i] : 0u, 0u);
+      } else {
+        const uint32_t h = SR ? mix32((uint32_t)o ^ ts) : 0u;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) S::template st1r<SR>(fout + i * a.plane + o, dA[i], h, i);
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty(s));
