@@ -277,6 +277,23 @@ def time_e2e(lbmp, torch, med, cfg, K):
     return dict(s=dt, h2d=3 * 8 * n, d2h=6 * 8 + 4)
 
 
+def reduce_max(value: float, device) -> float:
+    """Max over the ranks of the process group (the value itself for one rank)."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return float(value)
+
+
+def whole_job_glups(world_size: int, nodes_per_rank: int, steps: int, ms_slowest: float) -> float:
+    """Lattice updates of all replicas over the slowest rank's time (weak
+    scaling: every rank runs its own lattice of the same size)."""
+    return world_size * nodes_per_rank * steps / (ms_slowest * 1e-3) / 1e9
+
+
 def kernel_name(kernel: str, tag: str) -> str:
     staged = kernel == "staged" or (kernel == "auto" and tag == "StoreF16")
     return f"lbmp::staged_step_kernel<{tag}>" if staged else f"lbmp::step_kernel<{tag}>"
@@ -306,22 +323,16 @@ def run_ours(args, ws, rank, local):
     e2e = None if args.no_e2e else time_e2e(lbmp, torch, med, cfg, K)
 
     # slowest rank decides
-    ms = res["ms"]
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        if e2e:
-            t = torch.tensor([e2e["s"]], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e["s"] = float(t.item())
+    ms = reduce_max(res["ms"], "cuda")
+    if e2e:
+        e2e["s"] = reduce_max(e2e["s"], "cuda")
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
 
     nodes = res["nodes"]
-    glups = ws * nodes * K / (ms * 1e-3) / 1e9
+    glups = whole_job_glups(ws, nodes, K, ms)
     peak, peak_kind = measured_peaks()
     src = lbuild.source_hash()
 

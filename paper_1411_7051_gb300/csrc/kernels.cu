@@ -134,21 +134,28 @@ cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s) {
 // ------------------------------------------------- block reduction helper
 // Sums kNQ doubles over the block in a fixed order and writes them to
 // partials[blockLinear * kNQ + q] (deterministic for a fixed launch shape).
+// Quantities whose bit is set in max_mask are reduced by max (values >= 0).
 template <int BX>
-__device__ __forceinline__ void block_reduce_store(double v[kNQ], double *partials) {
+__device__ __forceinline__ void block_reduce_store(double v[kNQ], double *partials,
+                                                   unsigned max_mask = 0u) {
   __shared__ double red[BX / 32][kNQ];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < kNQ; ++q) {
+    const bool mx = (max_mask >> q) & 1u;
     double t = v[q];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, t, off);
+      t = mx ? fmax(t, o) : t + o;
+    }
     if (lane == 0) red[warp][q] = t;
   }
   __syncthreads();
   if (threadIdx.x < kNQ) {
+    const bool mx = (max_mask >> threadIdx.x) & 1u;
     double t = 0.0;
-    for (int w = 0; w < BX / 32; ++w) t += red[w][threadIdx.x];
+    for (int w = 0; w < BX / 32; ++w) t = mx ? fmax(t, red[w][threadIdx.x]) : t + red[w][threadIdx.x];
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
     partials[b * kNQ + threadIdx.x] = t;
   }
@@ -231,15 +238,21 @@ constexpr int kFinBX = 256;
 
 __global__ void __launch_bounds__(kFinBX)
     finalize_kernel(const double *__restrict__ partials, int nblocks, int nq,
-                    double *__restrict__ out) {
+                    double *__restrict__ out, unsigned max_mask) {
   __shared__ double sh[kFinBX];
   for (int q = 0; q < nq; ++q) {
+    const bool mx = (max_mask >> q) & 1u;
     double t = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += kFinBX) t += partials[(long long)b * nq + q];
+    for (int b = threadIdx.x; b < nblocks; b += kFinBX) {
+      const double v = partials[(long long)b * nq + q];
+      t = mx ? fmax(t, v) : t + v;
+    }
     sh[threadIdx.x] = t;
     __syncthreads();
     for (int w = kFinBX / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      if (threadIdx.x < w)
+        sh[threadIdx.x] = mx ? fmax(sh[threadIdx.x], sh[threadIdx.x + w])
+                             : sh[threadIdx.x] + sh[threadIdx.x + w];
       __syncthreads();
     }
     if (threadIdx.x == 0) out[q] = sh[0];
@@ -248,8 +261,8 @@ __global__ void __launch_bounds__(kFinBX)
 }
 
 cudaError_t launch_finalize(const double *partials, int nblocks, int nq, double *out,
-                            cudaStream_t s) {
-  finalize_kernel<<<1, kFinBX, 0, s>>>(partials, nblocks, nq, out);
+                            cudaStream_t s, unsigned max_mask) {
+  finalize_kernel<<<1, kFinBX, 0, s>>>(partials, nblocks, nq, out, max_mask);
   return cudaGetLastError();
 }
 
@@ -281,10 +294,14 @@ __global__ void __launch_bounds__(kMediumBX)
       out = make_float2((float)e, (float)inv_k);
       v[0] = e;
       v[1] = 1.0;
+      if (!flags && e > 0.0) {
+        if (inv_k > 0.0) v[2] = 1.0 / inv_k;  // largest finite k_a (max-reduced)
+        else v[3] = 1.0;                     // open pores (k_a = inf)
+      }
     }
     med[(long long)y * pitch + x] = out;
   }
-  block_reduce_store<kMediumBX>(v, partials);
+  block_reduce_store<kMediumBX>(v, partials, kMediumMaxMask);
 }
 
 int medium_blocks(int nx, int ny) { return ((nx + kMediumBX - 1) / kMediumBX) * ny; }

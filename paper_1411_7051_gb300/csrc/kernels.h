@@ -54,12 +54,15 @@ int macro_blocks(const StepArgs &a);
 cudaError_t launch_macro(int storage, const StepArgs &a, const void *fin,
                          const float2 *med, const MacroOut &o, cudaStream_t s);
 
-// Sum [nblocks][nq] partials in a fixed order into out[0..nq).
+// Reduce [nblocks][nq] partials in a fixed order into out[0..nq): by sum,
+// or by max for the quantities whose bit is set in max_mask.
 cudaError_t launch_finalize(const double *partials, int nblocks, int nq, double *out,
-                            cudaStream_t s);
+                            cudaStream_t s, unsigned max_mask = 0u);
 
 // Medium precompute: (eps, k_i, Kn) -> float2 (eps, 1/k_a); flags invalid
-// values in *bad; FP64 partial sums of eps over rows [y_lo, y_hi).
+// values in *bad; FP64 block partials over rows [y_lo, y_hi): sum eps, fluid
+// nodes, max finite k_a (max-reduced, kMediumMaxMask), open-pore count.
+constexpr unsigned kMediumMaxMask = 1u << 2;
 int medium_blocks(int nx, int ny);
 cudaError_t launch_medium(const double *eps, const double *k_i, const double *kn,
                           int nx, int ny, int pitch, int y_lo, int y_hi, float2 *med,

@@ -442,7 +442,7 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
                                 c->d_flag, c->partials, c->stream));
     c->launches++;
     LBMP_CK(lbmp::launch_finalize(c->partials, lbmp::medium_blocks(p.nx, p.ny), lbmp::kNQ,
-                                  c->results, c->stream));
+                                  c->results, c->stream, lbmp::kMediumMaxMask));
     c->launches++;
     unsigned flag = 0;
     LBMP_CK(cudaMemcpyAsync(c->h_results, c->results, lbmp::kNQ * sizeof(double),
@@ -461,16 +461,25 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
     c->eps_mean = c->h_results[0] / c->h_results[1];
     // storage scale S = 2^s for FP16: keep the expected largest deviation
     // near 2^10, far from both the FP16 overflow and its subnormal range.
+    // Velocity bound: the Darcy speed |G| max(k_a) / nu of the porous nodes,
+    // the Poiseuille speed |G| L^2 / (8 nu) if open pores exist, and at most
+    // 0.1 (beyond it the lattice leaves its low-Mach range anyway).
     if (p.storage == LBMP_STORE_FP16) {
       int s = p.fp16_log2_scale;
       if (s == 0) {
         double dev = 0.0;
         if (p.bc_x == LBMP_BCX_PRESSURE)
           dev = std::max(std::fabs(p.rho_in - p.rho0), std::fabs(p.rho_out - p.rho0));
-        const double L = (p.bc_y == LBMP_BCY_WALLS) ? (double)(p.ny - 2) : (double)std::max(p.nx, p.ny);
         const double nu = (p.tau - 0.5) / 3.0 / p.J;
         const double g = std::sqrt(p.Gx * p.Gx + p.Gy * p.Gy);
-        dev = std::max(dev, 3.0 * p.rho0 * g * L * L / (8.0 * nu));
+        const double kmax = c->h_results[2];
+        const bool open = c->h_results[3] > 0.0;
+        const double L = (p.bc_y == LBMP_BCY_WALLS) ? (double)(p.ny - 2)
+                                                    : (double)std::min(p.nx, p.ny);
+        double u = g * kmax / nu;
+        if (open) u = std::max(u, g * L * L / (8.0 * nu));
+        u = std::min(u, 0.1);
+        dev = std::max(dev, 3.0 * p.rho0 * u);
         dev = std::max(dev, 1e-7);
         s = (int)std::floor(std::log2(1024.0 / dev));
         s = std::min(60, std::max(-60, s));
