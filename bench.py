@@ -45,13 +45,19 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=4096)
-    ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32",
-                    help="storage of the headline value; the other one is reported beside it")
+    ap.add_argument("--storage", choices=["fp32", "fp16"], default=None,
+                    help="storage of the headline value (default fp32; fp16 for the batch "
+                         "workload); the other one is reported beside it")
     ap.add_argument("--no-other", action="store_true", help="skip the second storage run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fp16-rounding", choices=["stochastic", "nearest"], default="stochastic")
+    ap.add_argument("--workload", choices=["shale", "batch"], default="shale",
+                    help="shale: the 4096^2 fractured shale (default); batch: the batched sweep "
+                         "of two-component media of uneven sizes x Knudsen numbers")
+    ap.add_argument("--batch-media", type=int, default=256)
+    ap.add_argument("--batch-kn", type=int, default=8)
     ap.add_argument("--kernel", choices=["auto", "staged", "direct"], default="auto",
                     help="implementation of the step kernel (auto: direct for FP32 storage, "
                          "staged for FP16)")
@@ -310,7 +316,8 @@ def run_ours(args, ws, rank, local):
     lbmp.load()
     K, W = args.steps, max(3, args.warmup)
     med, cfg = workload(args.size)
-    primary = args.storage
+    primary = args.storage or "fp32"
+    args.storage = primary
     other = "fp16" if primary == "fp32" else "fp32"
 
     with ClockSampler(local) as clk:
@@ -382,11 +389,100 @@ def run_ours(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
+BATCH_SIDES = (256, 384, 512, 768, 1024)
+
+
+def batch_media(n_media: int, seed0: int = 1000):
+    """Seeded two-component media (correlation length 32, matrix eps 0.2 /
+    k_i 1e-5, inclusions eps 0.6 / k_i 1e-3) with sides drawn uniformly from
+    BATCH_SIDES; Kn is set per instance."""
+    import numpy as np
+    from paper_1411_7051_gb300 import media
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    sides = rng.choice(BATCH_SIDES, size=n_media)
+    return [media.two_component(int(n), seed=seed0 + m, corr_len=32.0) for m, n in enumerate(sides)]
+
+
+def run_batch(args, ws, rank, local):
+    """One persistent launch per step over every (medium, Kn) instance."""
+    import numpy as np
+    import torch
+    from paper_1411_7051_gb300 import lbmp
+    torch.cuda.set_device(local)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl")
+    K, W = args.steps, max(3, args.warmup)
+    t0 = time.perf_counter()
+    meds = batch_media(args.batch_media)
+    kns = np.logspace(-3, 1, args.batch_kn)
+    sizes = [(m.eps.shape[1], m.eps.shape[0]) for m in meds for _ in kns]
+    storage = lbmp.STORE_FP32 if args.storage == "fp32" else lbmp.STORE_FP16
+    cfg = lbmp.SimConfig(1, 1, tau=0.8, bc_x=lbmp.BCX_PRESSURE, bc_y=lbmp.BCY_WALLS,
+                         rho_in=1.0005, rho_out=0.9995, forchheimer=1, storage=storage,
+                         fp16_rounding=(lbmp.ROUND_STOCHASTIC if args.fp16_rounding == "stochastic"
+                                        else lbmp.ROUND_NEAREST))
+    b = lbmp.Batch(cfg, sizes)
+    j = 0
+    for m in meds:
+        for kn in kns:
+            b.set_fields(j, m.eps, m.k_i, np.full(m.eps.shape, kn))
+            j += 1
+    setup_s = time.perf_counter() - t0
+    chosen, tune_ms = b.tune(steps=5)
+    b.step(W)
+    b.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        l0 = b.info().launches
+        e0.record(b.stream)
+        b.step(K)
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+    ms = reduce_max(e0.elapsed_time(e1), "cuda")
+    info = b.info()
+    kg, _ = b.permeability()
+    if rank == 0:
+        nodes = int(info.total_nodes)
+        glups = whole_job_glups(ws, nodes, K, ms)
+        peak, kind = measured_peaks()
+        achieved = info.bytes_per_update * nodes / (ms * 1e-3 / K) / 1e9
+        line = {
+            "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": K,
+            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched sweep: {args.batch_media} two-component media "
+                                   f"(sides {list(BATCH_SIDES)}) x {args.batch_kn} Kn in [1e-3, 10], "
+                                   "pressure x, walls y, Forchheimer on, one persistent launch per step",
+                       "instances": len(sizes), "nodes": nodes,
+                       "storage": "fp16" if storage == lbmp.STORE_FP16 else "fp32",
+                       "shape": [info.shape_threads, info.shape_nodes_per_thread,
+                                 "persistent" if info.persistent else "one block per item"],
+                       "l2": "inputs larger than L2, no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": f"of {kind}",
+                         "bytes_per_update": info.bytes_per_update, "traffic": None,
+                         "kernel": "lbmp::batch_step_kernel"},
+            "gpu_launches": int(info.launches - l0), "clocks": clk.summary(),
+            "setup_s": setup_s, "tuned_shape_index": chosen, "tune_ms_per_step": tune_ms,
+            "k_g_range": [float(np.min(kg)), float(np.max(kg))],
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batch":
+        run_batch(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -183,6 +183,55 @@ lbmp_status lbmp_set_state(lbmp_ctx *ctx, const void *buf, size_t bytes, int32_t
 /* Sizes, storage and counters of ctx. */
 lbmp_status lbmp_get_info(lbmp_ctx *ctx, lbmp_info *out);
 
+/* ---------------------------------------------------------------------
+ * Batched sweeps.  `count` lattices of their own sizes (e.g. media
+ * realizations x Knudsen numbers) share the physics parameters of p (tau, J,
+ * G, boundary kinds, densities, Forchheimer, storage, rounding, seed; p->nx,
+ * p->ny and p->kernel are ignored) and advance together: one launch per time
+ * step covers a work list of row segments of all instances, either one block
+ * per segment or a persistent grid walking it (CUDA graphs of 32 steps).  Each instance has its own populations, medium
+ * and FP16 scale; the arithmetic per node is that of lbmp_step (Section III,
+ * Eq. 12-17).  The launch shape (threads per block x nodes per thread) is
+ * (threads per block x nodes per thread x grid mode) is chosen by
+ * lbmp_batch_tune.
+ * --------------------------------------------------------------------- */
+typedef struct lbmp_batch lbmp_batch;
+
+typedef struct lbmp_batch_info {
+  int32_t count;
+  int32_t shape_threads;          /* launch shape in use */
+  int32_t shape_nodes_per_thread;
+  int32_t persistent;             /* 1: persistent grid, 0: one block per work item */
+  int64_t total_nodes;            /* lattice updates per time step */
+  int64_t steps;
+  int64_t launches;
+  int64_t device_bytes;
+  double bytes_per_update;        /* algorithmic HBM bytes per lattice update */
+} lbmp_batch_info;
+
+/* Validate every (nx[i], ny[i]) with p under the rules of lbmp_create and
+ * allocate all instances.  Errors: EINVAL, ENOMEM, ECUDA. */
+lbmp_status lbmp_batch_create(const lbmp_params *p, int32_t count, const int32_t *nx,
+                              const int32_t *ny, lbmp_batch **out);
+lbmp_status lbmp_batch_destroy(lbmp_batch *b);
+/* Medium of instance i ([ny_i][nx_i] float64, as lbmp_set_fields), restart
+ * it from rest. */
+lbmp_status lbmp_batch_set_fields(lbmp_batch *b, int32_t i, const double *eps, const double *k_i,
+                                  const double *kn, int32_t where);
+/* n time steps of every instance; ESTATE until every instance has fields. */
+lbmp_status lbmp_batch_step(lbmp_batch *b, int64_t n);
+lbmp_status lbmp_batch_synchronize(lbmp_batch *b);
+/* Global permeability and <u_x> of every instance (host arrays of count
+ * doubles; either may be NULL), FP64 segmented reductions.  Synchronous. */
+lbmp_status lbmp_batch_permeability(lbmp_batch *b, double *k_g, double *u_mean);
+/* Post-stream populations of instance i, [9][ny_i][nx_i] float64. */
+lbmp_status lbmp_batch_populations(lbmp_batch *b, int32_t i, double *f, int32_t where);
+/* Autotuner: time `steps` steps of every candidate launch shape on this
+ * batch, keep the fastest, restore the populations and time level.  Returns
+ * the chosen candidate index and its time per step (either may be NULL). */
+lbmp_status lbmp_batch_tune(lbmp_batch *b, int32_t steps, int32_t *chosen, double *ms_per_step);
+lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out);
+
 /* Global permeability of a lattice state held entirely in caller memory,
  * allocating nothing.  The paper has no counterpart: this serves callers
  * that cannot call cudaMalloc -- code that runs while another component

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbmp.so")
-SOURCES = ["kernels.cu", "lbmp_api.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "lbmp_api.cu", "noalloc.cu", "batch.cu"]
 HEADERS = ["lattice.cuh", "kernels.h", "staged.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

@@ -1,0 +1,828 @@
+// Batched sweeps: many lattices (media realizations, Knudsen numbers, sizes)
+// advanced together by one persistent launch per time step.
+//
+// Every instance has its own population buffers, medium and FP16 scale; the
+// physics parameters (tau, J, G, boundary kinds, densities, Forchheimer) are
+// shared.  The step kernel is the fused pull-collide-store of Eq. 12-17
+// (Section III) over a flat work list: work item w is a row segment of
+// BX * NPT nodes of instance item_inst[w].  Either one block per item, or a
+// persistent grid (SMs x resident blocks) walking contiguous item ranges.
+// The launch shape (BX, NPT, grid mode) is picked by lbmp_batch_tune, which
+// times every candidate on the batch itself and restores the populations.
+// Per-instance global permeabilities are FP64 segmented reductions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "lattice.cuh"
+#include "lbmp.h"
+
+namespace lbmp {
+
+struct BatchInst {
+  StepArgs a;            // geometry (y0 = first fluid row), physics, FP16 scale
+  void *buf[2];          // population buffers
+  const float2 *med;     // (eps, 1/k_a)
+  int rows;              // fluid rows
+  int index;             // instance number (mixes the stochastic-rounding stream)
+};
+
+__device__ __forceinline__ int find_instance(const long long *__restrict__ cum, int count,
+                                             long long w) {
+  int lo = 0, hi = count;  // cum[0] = 0, cum[count] = items; largest lo with cum[lo] <= w
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (cum[mid] <= w) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// One work item: a row segment of BX * NPT nodes of instance ii.
+template <class S, bool SR, int BX, int NPT>
+__device__ __forceinline__ void batch_item(const BatchInst &I, long long local, int parity,
+                                           uint32_t ts) {
+  const StepArgs &a = I.a;
+  constexpr int chunk = BX * NPT;
+  const int xblocks = (a.nx + chunk - 1) / chunk;
+  const int y = a.y0 + (int)(local / xblocks);
+  const int xb = (int)(local % xblocks) * chunk + threadIdx.x;
+  const typename S::T *fin = (const typename S::T *)I.buf[parity];
+  typename S::T *fout = (typename S::T *)I.buf[parity ^ 1];
+  const long long row = (long long)y * a.pitch;
+  float d[NPT][9];
+  float2 m[NPT];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int x = xb + j * BX;
+    if (x < a.nx) {
+      pull_node<S>(fin, a, x, y, d[j]);
+      m[j] = I.med[row + x];
+    }
+  }
+  const uint32_t tsi = SR ? ts ^ mix32((uint32_t)I.index * 0x85ebca77u + 1u) : 0u;
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int x = xb + j * BX;
+    if (x >= a.nx) continue;
+    if (a.pressure && (x == 0 || x == a.nx - 1))
+      pressure_node<S>(fin, I.med, a, x, y, m[j].x, d[j]);
+    const NodeState s = node_state(d[j], m[j].x, m[j].y, a);
+    collide<S::kHiLo>(d[j], s, a);
+    typename S::T *o = fout + row + x;
+    const uint32_t h = SR ? mix32((uint32_t)(row + x) ^ tsi) : 0u;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) S::template st1r<SR>(o + i * a.plane, d[j][i], h, i);
+  }
+}
+
+// persistent = 0: block b updates work item b (one launch over every item).  persistent = 1: gridDim.x
+// resident blocks each walk a contiguous range of items.  item_inst[w] is
+// the instance of item w, cum[i] its first item.
+template <class S, bool SR, int BX, int NPT>
+__global__ void __launch_bounds__(BX)
+    batch_step_kernel(const BatchInst *__restrict__ inst, const long long *__restrict__ cum,
+                      const int *__restrict__ item_inst, long long items, int persistent,
+                      int parity, const unsigned long long *__restrict__ tctr, int k) {
+  uint32_t ts = 0;
+  if (SR) {
+    const StepArgs &a0 = inst[0].a;
+    const unsigned long long t = *tctr + (unsigned long long)k;
+    ts = mix32((uint32_t)t * 0x9e3779b9u ^ a0.seed_lo ^ mix32((uint32_t)(t >> 32) ^ a0.seed_hi));
+  }
+  if (!persistent) {
+    const long long w = blockIdx.x;
+    if (w >= items) return;
+    const int ii = item_inst[w];
+    batch_item<S, SR, BX, NPT>(inst[ii], w - cum[ii], parity, ts);
+    return;
+  }
+  const long long per = (items + gridDim.x - 1) / gridDim.x;
+  const long long w0 = (long long)blockIdx.x * per;
+  const long long w1 = w0 + per < items ? w0 + per : items;
+  for (long long w = w0; w < w1; ++w) {
+    const int ii = item_inst[w];
+    batch_item<S, SR, BX, NPT>(inst[ii], w - cum[ii], parity, ts);
+  }
+}
+
+// Per-instance reductions: block partials over the work list (one 256-node
+// segment per item), then one block per instance sums its items in order.
+constexpr int kBatchMacroBX = 256;
+
+template <class S>
+__global__ void __launch_bounds__(kBatchMacroBX)
+    batch_macro_kernel(const BatchInst *__restrict__ inst, const long long *__restrict__ cum,
+                       int count, int parity, double *__restrict__ partials) {
+  const long long items = cum[count];
+  for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+    const int ii = find_instance(cum, count, w);
+    const BatchInst &I = inst[ii];
+    const StepArgs &a = I.a;
+    const long long local = w - cum[ii];
+    const int xblocks = (a.nx + kBatchMacroBX - 1) / kBatchMacroBX;
+    const int y = a.y0 + (int)(local / xblocks);
+    const int x = (int)(local % xblocks) * kBatchMacroBX + threadIdx.x;
+    const typename S::T *fin = (const typename S::T *)I.buf[parity];
+    double v[kNQ] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (x < a.nx) {
+      float d[9];
+      const float2 m = I.med[(long long)y * a.pitch + x];
+      pull_node<S>(fin, a, x, y, d);
+      if (a.pressure && (x == 0 || x == a.nx - 1)) pressure_node<S>(fin, I.med, a, x, y, m.x, d);
+      const NodeState s = node_state(d, m.x, m.y, a);
+      const bool finite = isfinite(s.ux) && isfinite(s.uy) && isfinite(s.rho);
+      v[0] = finite ? (double)s.ux : 0.0;
+      v[1] = finite ? (double)s.uy : 0.0;
+      v[2] = finite ? (double)(s.drho_s * a.inv_scale) : 0.0;
+      v[3] = finite ? (double)s.ux * s.ux + (double)s.uy * s.uy : 0.0;
+      v[5] = finite ? 0.0 : 1.0;
+    }
+    __shared__ double red[kBatchMacroBX / 32][kNQ];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) {
+      double t = v[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+      if (lane == 0) red[warp][q] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNQ) {
+      double t = 0.0;
+      for (int ww = 0; ww < kBatchMacroBX / 32; ++ww) t += red[ww][threadIdx.x];
+      partials[w * kNQ + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    batch_finalize_kernel(const long long *__restrict__ cum, const double *__restrict__ partials,
+                          double *__restrict__ out) {
+  __shared__ double sh[256];
+  const int ii = blockIdx.x;
+  const long long b0 = cum[ii], b1 = cum[ii + 1];
+  for (int q = 0; q < kNQ; ++q) {
+    double t = 0.0;
+    for (long long b = b0 + threadIdx.x; b < b1; b += 256) t += partials[b * kNQ + q];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(long long)ii * kNQ + q] = sh[0];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ launch shapes
+struct Shape {
+  int bx, npt, persistent;
+};
+constexpr Shape kShapes[] = {{128, 1, 0}, {128, 2, 0}, {256, 1, 0}, {256, 2, 0}, {64, 4, 0},
+                             {128, 4, 0}, {128, 2, 1}, {256, 2, 1}, {64, 4, 1}};
+constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+
+template <class S, bool SR, int BX, int NPT>
+static cudaError_t launch_shape_t(const BatchInst *inst, const long long *cum, const int *item_inst,
+                                  int persistent, int parity, const unsigned long long *tctr, int k,
+                                  int nsm, long long items, cudaStream_t s) {
+  // resident blocks per SM of this instantiation (queried once per process)
+  static const int per_sm = [] {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batch_step_kernel<S, SR, BX, NPT>, BX,
+                                                      0) != cudaSuccess)
+      v = 1;
+    return std::max(v, 1);
+  }();
+  long long grid = persistent ? std::min((long long)per_sm * nsm, items) : items;
+  if (grid < 1) return cudaSuccess;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  batch_step_kernel<S, SR, BX, NPT><<<(unsigned)grid, BX, 0, s>>>(inst, cum, item_inst, items,
+                                                                   persistent, parity, tctr, k);
+  return cudaGetLastError();
+}
+
+template <class S, bool SR>
+static cudaError_t launch_shape_s(int shape, const BatchInst *inst, const long long *cum,
+                                  const int *item_inst, int parity,
+                                  const unsigned long long *tctr, int k, int nsm, long long items,
+                                  cudaStream_t s) {
+  const int ps = kShapes[shape].persistent;
+  switch (kShapes[shape].bx * 16 + kShapes[shape].npt) {
+    case 128 * 16 + 1: return launch_shape_t<S, SR, 128, 1>(inst, cum, item_inst, ps, parity, tctr, k, nsm, items, s);
+    case 128 * 16 + 2: return launch_shape_t<S, SR, 128, 2>(inst, cum, item_inst, ps, parity, tctr, k, nsm, items, s);
+    case 256 * 16 + 1: return launch_shape_t<S, SR, 256, 1>(inst, cum, item_inst, ps, parity, tctr, k, nsm, items, s);
+    case 256 * 16 + 2: return launch_shape_t<S, SR, 256, 2>(inst, cum, item_inst, ps, parity, tctr, k, nsm, items, s);
+    case 64 * 16 + 4: return launch_shape_t<S, SR, 64, 4>(inst, cum, item_inst, ps, parity, tctr, k, nsm, items, s);
+    default: return launch_shape_t<S, SR, 128, 4>(inst, cum, item_inst, ps, parity, tctr, k, nsm, items, s);
+  }
+}
+
+static cudaError_t launch_batch_step(int storage, bool sr, int shape, const BatchInst *inst,
+                                     const long long *cum, const int *item_inst, int parity,
+                                     const unsigned long long *tctr, int k, int nsm,
+                                     long long items, cudaStream_t s) {
+  if (storage == LBMP_STORE_FP32)
+    return launch_shape_s<StoreF32, false>(shape, inst, cum, item_inst, parity, tctr, k, nsm, items, s);
+  if (sr)
+    return launch_shape_s<StoreF16, true>(shape, inst, cum, item_inst, parity, tctr, k, nsm, items, s);
+  return launch_shape_s<StoreF16, false>(shape, inst, cum, item_inst, parity, tctr, k, nsm, items, s);
+}
+
+}  // namespace lbmp
+
+using lbmp::BatchInst;
+
+namespace {
+
+lbmp_status bfail(lbmp_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  lbmp::set_last_error(buf);
+  return st;
+}
+
+lbmp_status bcuda(cudaError_t e, const char *what) {
+  cudaGetLastError();
+  return bfail(e == cudaErrorMemoryAllocation ? LBMP_ENOMEM : LBMP_ECUDA, "%s: %s", what,
+               cudaGetErrorString(e));
+}
+
+#define BCK(call)                                        \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return bcuda(e_, #call);      \
+  } while (0)
+
+constexpr int kBatchGraphSteps = 32;
+
+}  // namespace
+
+struct lbmp_batch {
+  lbmp_params p{};
+  int device = 0, nsm = 1;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  bool own_stream = false;
+  int count = 0;
+  bool sr = false;
+  std::vector<BatchInst> h_inst;
+  std::vector<int> fields_set;
+  std::vector<double> eps_mean;
+  std::vector<long long> fluid_nodes;
+  BatchInst *d_inst = nullptr;
+  long long *d_cum_step = nullptr;   // work list of the chosen shape
+  int *d_item_inst = nullptr;        // instance of every work item (chosen shape)
+  long long items_cap = 0;           // capacity of d_item_inst
+  long long *d_cum_macro = nullptr;  // work list of the reductions
+  long long items_step = 0, items_macro = 0;
+  double *d_partials = nullptr;      // [items_macro][kNQ]
+  double *d_results = nullptr;       // [count][kNQ]
+  double *d_med_partials = nullptr;  // set_fields scratch
+  double *d_med_results = nullptr;
+  unsigned *d_flag = nullptr;
+  unsigned long long *d_tctr = nullptr;
+  int shape = 1;                     // index into kShapes (default 128 x 2)
+  int parity = 0;
+  int64_t steps = 0, launches = 0, total_nodes = 0, device_bytes = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+lbmp_status balloc(lbmp_batch *b, void **p, size_t bytes, const char *what) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return bcuda(e, what);
+  }
+  b->allocs.push_back(*p);
+  b->device_bytes += (int64_t)bytes;
+  return LBMP_OK;
+}
+
+void bfree_graphs(lbmp_batch *b) {
+  for (auto &g : b->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+void brelease(lbmp_batch *b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  bfree_graphs(b);
+  for (void *p : b->allocs) cudaFree(p);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// cumulative work items for a chunk of `chunk` nodes per item
+std::vector<long long> work_list(const lbmp_batch *b, int chunk) {
+  std::vector<long long> cum(b->count + 1, 0);
+  for (int i = 0; i < b->count; ++i) {
+    const lbmp::StepArgs &a = b->h_inst[i].a;
+    const long long xblocks = (a.nx + chunk - 1) / chunk;
+    cum[i + 1] = cum[i] + xblocks * (long long)b->h_inst[i].rows;
+  }
+  return cum;
+}
+
+lbmp_status upload_cum(lbmp_batch *b, long long *d_cum, const std::vector<long long> &cum) {
+  BCK(cudaMemcpyAsync(d_cum, cum.data(), cum.size() * sizeof(long long),
+                      cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  return LBMP_OK;
+}
+
+lbmp_status set_shape(lbmp_batch *b, int shape) {
+  const lbmp::Shape sh = lbmp::kShapes[shape];
+  std::vector<long long> cum = work_list(b, sh.bx * sh.npt);
+  if (cum.back() > b->items_cap) return bfail(LBMP_ECUDA, "work-item table too small");
+  std::vector<int> item_inst((size_t)cum.back());
+  for (int i = 0; i < b->count; ++i)
+    std::fill(item_inst.begin() + cum[i], item_inst.begin() + cum[i + 1], i);
+  BCK(cudaMemcpyAsync(b->d_item_inst, item_inst.data(), item_inst.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, b->stream));
+  lbmp_status st = upload_cum(b, b->d_cum_step, cum);
+  if (st) return st;
+  b->items_step = cum.back();
+  b->shape = shape;
+  bfree_graphs(b);
+  return LBMP_OK;
+}
+
+lbmp_status launch_steps(lbmp_batch *b, int64_t n, cudaStream_t s, bool count_launches) {
+  for (int64_t t = 0; t < n; ++t) {
+    BCK(lbmp::launch_batch_step(b->p.storage, b->sr, b->shape, b->d_inst, b->d_cum_step,
+                                b->d_item_inst, b->parity, b->d_tctr, (int)t, b->nsm,
+                                b->items_step, s));
+    b->parity ^= 1;
+    if (count_launches) b->launches++;
+  }
+  if (n > 0 && b->sr) {
+    BCK(lbmp::launch_bump(b->d_tctr, (int)n, s));
+    if (count_launches) b->launches++;
+  }
+  return LBMP_OK;
+}
+
+lbmp_status get_graph(lbmp_batch *b, cudaGraphExec_t *out) {
+  const int par = b->parity;
+  if (b->graph[par]) {
+    *out = b->graph[par];
+    return LBMP_OK;
+  }
+  cudaGraph_t g = nullptr;
+  BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  lbmp_status st = launch_steps(b, kBatchGraphSteps, b->cap_stream, false);
+  cudaError_t end = cudaStreamEndCapture(b->cap_stream, &g);
+  b->parity = par;  // the capture did not run anything
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (end != cudaSuccess) return bcuda(end, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return bcuda(ie, "cudaGraphInstantiate");
+  b->graph[par] = exec;
+  *out = exec;
+  return LBMP_OK;
+}
+
+lbmp_status do_step(lbmp_batch *b, int64_t n) {
+  int64_t left = n;
+  while (left >= kBatchGraphSteps) {
+    cudaGraphExec_t g = nullptr;
+    lbmp_status st = get_graph(b, &g);
+    if (st) return st;
+    BCK(cudaGraphLaunch(g, b->stream));
+    b->launches += kBatchGraphSteps + (b->sr ? 1 : 0);
+    left -= kBatchGraphSteps;
+    // an even number of steps keeps the parity
+  }
+  lbmp_status st = launch_steps(b, left, b->stream, true);
+  if (st) return st;
+  b->steps += n;
+  return LBMP_OK;
+}
+
+bool all_fields(const lbmp_batch *b) {
+  for (int f : b->fields_set)
+    if (!f) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32_t *nx,
+                              const int32_t *ny, lbmp_batch **out) {
+  try {
+    if (!pin || !nx || !ny || !out) return bfail(LBMP_EINVAL, "lbmp_batch_create: NULL argument");
+    *out = nullptr;
+    if (count < 1) return bfail(LBMP_EINVAL, "count must be >= 1");
+    lbmp_params p = *pin;
+    if (p.J == 0.0) p.J = 1.0;
+    if (p.rho0 == 0.0) p.rho0 = 1.0;
+    // validate the shared parameters through the single-lattice rules
+    for (int i = 0; i < count; ++i) {
+      lbmp_params q = p;
+      q.nx = nx[i];
+      q.ny = ny[i];
+      q.stream = nullptr;
+      q.kernel = LBMP_KERNEL_DIRECT;
+      lbmp_status st = lbmp::validate_params(&q);
+      if (st) return st;
+    }
+    lbmp_batch *b = new (std::nothrow) lbmp_batch();
+    if (!b) return bfail(LBMP_ENOMEM, "host allocation of the batch");
+    b->p = p;
+    b->count = count;
+    b->sr = p.storage == LBMP_STORE_FP16 && p.fp16_rounding == LBMP_ROUND_STOCHASTIC;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) {
+      delete b;
+      return bcuda(e, "device query");
+    }
+    lbmp_status st = LBMP_OK;
+#define BTRY(x)           \
+  do {                    \
+    st = (x);             \
+    if (st != LBMP_OK) {  \
+      brelease(b);        \
+      return st;          \
+    }                     \
+  } while (0)
+    if (p.stream) {
+      b->stream = (cudaStream_t)p.stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) BTRY(bcuda(e, "cudaStreamCreate"));
+      b->own_stream = true;
+    }
+    e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) BTRY(bcuda(e, "cudaStreamCreate (capture)"));
+    const size_t elem = p.storage == LBMP_STORE_FP32 ? 4 : 2;
+    b->h_inst.resize(count);
+    b->fields_set.assign(count, 0);
+    b->eps_mean.assign(count, 1.0);
+    b->fluid_nodes.assign(count, 0);
+    for (int i = 0; i < count; ++i) {
+      BatchInst &I = b->h_inst[i];
+      std::memset(&I, 0, sizeof(I));
+      lbmp::StepArgs &a = I.a;
+      const int walls = p.bc_y == LBMP_BCY_WALLS;
+      a.nx = nx[i];
+      a.ny = ny[i];
+      a.pitch = ((nx[i] + 63) / 64) * 64;
+      a.y0 = walls ? 1 : 0;
+      a.plane = (long long)a.pitch * ny[i];
+      a.rho0 = (float)p.rho0;
+      a.drho_in = (float)(p.rho_in - p.rho0);
+      a.drho_out = (float)(p.rho_out - p.rho0);
+      a.omega = (float)(1.0 / p.tau);
+      a.one_m_omega = (float)(1.0 - 1.0 / p.tau);
+      a.cforce = (float)(1.0 - 0.5 / p.tau);
+      a.nu = (float)((p.tau - 0.5) / 3.0 / p.J);
+      a.Gx = (float)p.Gx;
+      a.Gy = (float)p.Gy;
+      a.fe_half = (float)(0.5 * 1.75 / std::sqrt(150.0));
+      a.scale = 1.0f;
+      a.inv_scale = 1.0f;
+      a.walls = walls;
+      a.pressure = p.bc_x == LBMP_BCX_PRESSURE;
+      a.forch = p.forchheimer != 0;
+      a.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
+      a.seed_hi = (uint32_t)(p.seed >> 32);
+      a.test_drop_tile = -1;
+      I.rows = walls ? ny[i] - 2 : ny[i];
+      I.index = i;
+      b->fluid_nodes[i] = (long long)nx[i] * I.rows;
+      b->total_nodes += b->fluid_nodes[i];
+      const size_t pop_bytes = (size_t)a.plane * 9 * elem;
+      BTRY(balloc(b, &I.buf[0], pop_bytes, "batch populations A"));
+      BTRY(balloc(b, &I.buf[1], pop_bytes, "batch populations B"));
+      void *m = nullptr;
+      BTRY(balloc(b, &m, (size_t)a.plane * sizeof(float2), "batch medium"));
+      I.med = (const float2 *)m;
+    }
+    const std::vector<long long> cum_macro = work_list(b, lbmp::kBatchMacroBX);
+    b->items_macro = cum_macro.back();
+    BTRY(balloc(b, (void **)&b->d_inst, sizeof(BatchInst) * count, "batch descriptors"));
+    BTRY(balloc(b, (void **)&b->d_cum_step, sizeof(long long) * (count + 1), "work list"));
+    BTRY(balloc(b, (void **)&b->d_cum_macro, sizeof(long long) * (count + 1), "work list"));
+    {
+      int min_chunk = 1 << 30;
+      for (const auto &sh : lbmp::kShapes) min_chunk = std::min(min_chunk, sh.bx * sh.npt);
+      b->items_cap = work_list(b, min_chunk).back();
+      BTRY(balloc(b, (void **)&b->d_item_inst, sizeof(int) * (size_t)b->items_cap, "work-item table"));
+    }
+    BTRY(balloc(b, (void **)&b->d_partials, sizeof(double) * lbmp::kNQ * (size_t)b->items_macro,
+                "batch partials"));
+    BTRY(balloc(b, (void **)&b->d_results, sizeof(double) * lbmp::kNQ * count, "batch results"));
+    int max_mb = 0;
+    for (int i = 0; i < count; ++i) max_mb = std::max(max_mb, lbmp::medium_blocks(nx[i], ny[i]));
+    BTRY(balloc(b, (void **)&b->d_med_partials, sizeof(double) * lbmp::kNQ * max_mb, "medium partials"));
+    BTRY(balloc(b, (void **)&b->d_med_results, sizeof(double) * lbmp::kNQ, "medium results"));
+    BTRY(balloc(b, (void **)&b->d_flag, sizeof(unsigned), "validation flag"));
+    BTRY(balloc(b, (void **)&b->d_tctr, sizeof(unsigned long long), "time-level counter"));
+    e = cudaMemset(b->d_tctr, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) BTRY(bcuda(e, "cudaMemset"));
+    BTRY(upload_cum(b, b->d_cum_macro, cum_macro));
+    BTRY(set_shape(b, b->shape));
+#undef BTRY
+    *out = b;
+    return LBMP_OK;
+  } catch (...) {
+    return bfail(LBMP_ECUDA, "lbmp_batch_create: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_batch_destroy(lbmp_batch *b) {
+  brelease(b);
+  return LBMP_OK;
+}
+
+lbmp_status lbmp_batch_set_fields(lbmp_batch *b, int32_t i, const double *eps, const double *k_i,
+                                  const double *kn, int32_t where) {
+  try {
+    if (!b || !eps || !k_i || !kn) return bfail(LBMP_EINVAL, "lbmp_batch_set_fields: NULL argument");
+    if (i < 0 || i >= b->count) return bfail(LBMP_EINVAL, "instance %d out of range", i);
+    if (where != LBMP_HOST && where != LBMP_DEVICE) return bfail(LBMP_EINVAL, "bad where");
+    BCK(cudaSetDevice(b->device));
+    BatchInst &I = b->h_inst[i];
+    lbmp::StepArgs &a = I.a;
+    const size_t n = (size_t)a.nx * a.ny;
+    const double *de = eps, *dk = k_i, *dn = kn;
+    void *tmp = nullptr;
+    if (where == LBMP_HOST) {
+      BCK(cudaMalloc(&tmp, 3 * n * sizeof(double)));
+      double *t = (double *)tmp;
+      cudaMemcpyAsync(t, eps, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+      cudaMemcpyAsync(t + n, k_i, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+      cudaMemcpyAsync(t + 2 * n, kn, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+      de = t;
+      dk = t + n;
+      dn = t + 2 * n;
+    }
+    const int y_hi = a.walls ? a.ny - 1 : a.ny;
+    unsigned flag = 0;
+    double res[lbmp::kNQ];
+    cudaError_t e = cudaMemsetAsync(b->d_flag, 0, sizeof(unsigned), b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync((void *)I.med, 0, (size_t)a.plane * sizeof(float2), b->stream);
+    if (e == cudaSuccess)
+      e = lbmp::launch_medium(de, dk, dn, a.nx, a.ny, a.pitch, a.y0, y_hi, (float2 *)I.med,
+                              b->d_flag, b->d_med_partials, b->stream);
+    if (e == cudaSuccess)
+      e = lbmp::launch_finalize(b->d_med_partials, lbmp::medium_blocks(a.nx, a.ny), lbmp::kNQ,
+                                b->d_med_results, b->stream, lbmp::kMediumMaxMask);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(res, b->d_med_results, sizeof(res), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&flag, b->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return bcuda(e, "batch medium precompute");
+    if (flag) {
+      b->fields_set[i] = 0;
+      return bfail(LBMP_EINVAL, "lbmp_batch_set_fields: invalid values in instance %d (flags %u)", i, flag);
+    }
+    b->eps_mean[i] = res[0] / res[1];
+    double scale = 1.0;
+    const lbmp_params &p = b->p;
+    if (p.storage == LBMP_STORE_FP16) {
+      int s = p.fp16_log2_scale;
+      if (s == 0) {  // the rule of lbmp_set_fields
+        double dev = 0.0;
+        if (p.bc_x == LBMP_BCX_PRESSURE)
+          dev = std::max(std::fabs(p.rho_in - p.rho0), std::fabs(p.rho_out - p.rho0));
+        const double nu = (p.tau - 0.5) / 3.0 / p.J;
+        const double g = std::sqrt(p.Gx * p.Gx + p.Gy * p.Gy);
+        const double L = a.walls ? (double)(a.ny - 2) : (double)std::min(a.nx, a.ny);
+        double u = g * res[2] / nu;
+        if (res[3] > 0.0) u = std::max(u, g * L * L / (8.0 * nu));
+        u = std::min(u, 0.1);
+        dev = std::max(std::max(dev, 3.0 * p.rho0 * u), 1e-7);
+        s = std::min(60, std::max(-60, (int)std::floor(std::log2(1024.0 / dev))));
+      }
+      scale = std::ldexp(1.0, s);
+    }
+    a.scale = (float)scale;
+    a.inv_scale = (float)(1.0 / scale);
+    const size_t elem = p.storage == LBMP_STORE_FP32 ? 4 : 2;
+    BCK(cudaMemsetAsync(I.buf[0], 0, (size_t)a.plane * 9 * elem, b->stream));
+    BCK(cudaMemsetAsync(I.buf[1], 0, (size_t)a.plane * 9 * elem, b->stream));
+    BCK(cudaMemcpyAsync(b->d_inst + i, &I, sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    b->fields_set[i] = 1;
+    bfree_graphs(b);
+    return LBMP_OK;
+  } catch (...) {
+    return bfail(LBMP_ECUDA, "lbmp_batch_set_fields: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_batch_step(lbmp_batch *b, int64_t n) {
+  try {
+    if (!b) return bfail(LBMP_EINVAL, "lbmp_batch_step: NULL batch");
+    if (n < 0) return bfail(LBMP_EINVAL, "n must be >= 0");
+    if (!all_fields(b)) return bfail(LBMP_ESTATE, "lbmp_batch_step: every instance needs its fields");
+    if (n == 0) return LBMP_OK;
+    BCK(cudaSetDevice(b->device));
+    return do_step(b, n);
+  } catch (...) {
+    return bfail(LBMP_ECUDA, "lbmp_batch_step: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_batch_synchronize(lbmp_batch *b) {
+  if (!b) return bfail(LBMP_EINVAL, "NULL batch");
+  BCK(cudaSetDevice(b->device));
+  BCK(cudaStreamSynchronize(b->stream));
+  return LBMP_OK;
+}
+
+lbmp_status lbmp_batch_permeability(lbmp_batch *b, double *k_g, double *u_mean) {
+  try {
+    if (!b) return bfail(LBMP_EINVAL, "NULL batch");
+    if (!all_fields(b)) return bfail(LBMP_ESTATE, "every instance needs its fields");
+    BCK(cudaSetDevice(b->device));
+    cudaError_t e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, lbmp::batch_macro_kernel<lbmp::StoreF32>, lbmp::kBatchMacroBX, 0);
+    if (e != cudaSuccess) return bcuda(e, "occupancy");
+    const long long grid = std::min<long long>((long long)std::max(per_sm, 1) * b->nsm, b->items_macro);
+    if (b->p.storage == LBMP_STORE_FP32)
+      lbmp::batch_macro_kernel<lbmp::StoreF32><<<(unsigned)grid, lbmp::kBatchMacroBX, 0, b->stream>>>(
+          b->d_inst, b->d_cum_macro, b->count, b->parity, b->d_partials);
+    else
+      lbmp::batch_macro_kernel<lbmp::StoreF16><<<(unsigned)grid, lbmp::kBatchMacroBX, 0, b->stream>>>(
+          b->d_inst, b->d_cum_macro, b->count, b->parity, b->d_partials);
+    BCK(cudaGetLastError());
+    lbmp::batch_finalize_kernel<<<b->count, 256, 0, b->stream>>>(b->d_cum_macro, b->d_partials,
+                                                                  b->d_results);
+    BCK(cudaGetLastError());
+    b->launches += 2;
+    std::vector<double> res((size_t)b->count * lbmp::kNQ);
+    BCK(cudaMemcpyAsync(res.data(), b->d_results, res.size() * sizeof(double),
+                        cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    const lbmp_params &p = b->p;
+    const double nu = (p.tau - 0.5) / 3.0 / p.J;
+    lbmp_status st = LBMP_OK;
+    for (int i = 0; i < b->count; ++i) {
+      const double *r = res.data() + (size_t)i * lbmp::kNQ;
+      if (r[5] != 0.0) st = bfail(LBMP_ENAN, "instance %d has non-finite velocities", i);
+      const double um = r[0] / (double)b->fluid_nodes[i];
+      double g = p.Gx;
+      if (p.bc_x == LBMP_BCX_PRESSURE)
+        g += (p.rho_in - p.rho_out) / 3.0 / b->eps_mean[i] /
+             (p.rho0 * (double)(b->h_inst[i].a.nx - 1));
+      if (u_mean) u_mean[i] = um;
+      if (k_g) k_g[i] = nu * um / g;
+    }
+    return st;
+  } catch (...) {
+    return bfail(LBMP_ECUDA, "lbmp_batch_permeability: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_batch_populations(lbmp_batch *b, int32_t i, double *f, int32_t where) {
+  try {
+    if (!b || !f) return bfail(LBMP_EINVAL, "NULL argument");
+    if (i < 0 || i >= b->count) return bfail(LBMP_EINVAL, "instance %d out of range", i);
+    if (!b->fields_set[i]) return bfail(LBMP_ESTATE, "instance %d has no fields", i);
+    BCK(cudaSetDevice(b->device));
+    const BatchInst &I = b->h_inst[i];
+    lbmp::StepArgs a = I.a;
+    a.y0 = 0;
+    const size_t n = (size_t)a.nx * a.ny * 9;
+    double *dst = f;
+    void *tmp = nullptr;
+    if (where == LBMP_HOST) {
+      BCK(cudaMalloc(&tmp, n * sizeof(double)));
+      dst = (double *)tmp;
+    }
+    lbmp::MacroOut o{};
+    o.pops = dst;
+    cudaError_t e = lbmp::launch_macro(b->p.storage, a, I.buf[b->parity], I.med, o, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess && tmp) e = cudaMemcpy(f, tmp, n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return bcuda(e, "batch populations");
+    return LBMP_OK;
+  } catch (...) {
+    return bfail(LBMP_ECUDA, "lbmp_batch_populations: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_batch_tune(lbmp_batch *b, int32_t steps, int32_t *chosen, double *ms_per_step) {
+  try {
+    if (!b) return bfail(LBMP_EINVAL, "NULL batch");
+    if (steps < 1) return bfail(LBMP_EINVAL, "steps must be >= 1");
+    if (!all_fields(b)) return bfail(LBMP_ESTATE, "every instance needs its fields");
+    BCK(cudaSetDevice(b->device));
+    const size_t elem = b->p.storage == LBMP_STORE_FP32 ? 4 : 2;
+    // save the current populations and the counter of every instance
+    std::vector<void *> saved(b->count, nullptr);
+    size_t total = 0;
+    for (int i = 0; i < b->count; ++i) total += (size_t)b->h_inst[i].a.plane * 9 * elem;
+    void *store = nullptr;
+    BCK(cudaMalloc(&store, total));
+    size_t off = 0;
+    for (int i = 0; i < b->count; ++i) {
+      const size_t bytes = (size_t)b->h_inst[i].a.plane * 9 * elem;
+      saved[i] = (char *)store + off;
+      cudaMemcpyAsync(saved[i], b->h_inst[i].buf[b->parity], bytes, cudaMemcpyDeviceToDevice, b->stream);
+      off += bytes;
+    }
+    unsigned long long tctr0 = 0;
+    cudaMemcpyAsync(&tctr0, b->d_tctr, sizeof(tctr0), cudaMemcpyDeviceToHost, b->stream);
+    const int parity0 = b->parity;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = b->shape;
+    float best_ms = 1e30f;
+    lbmp_status st = LBMP_OK;
+    for (int sidx = 0; sidx < lbmp::kNumShapes && st == LBMP_OK; ++sidx) {
+      st = set_shape(b, sidx);
+      if (st) break;
+      st = launch_steps(b, 2, b->stream, false);  // warm-up
+      if (st) break;
+      cudaEventRecord(e0, b->stream);
+      st = launch_steps(b, steps, b->stream, false);
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = bcuda(cudaGetLastError(), "tuning run");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = sidx;
+      }
+    }
+    // restore the state
+    b->parity = parity0;
+    off = 0;
+    for (int i = 0; i < b->count; ++i) {
+      const size_t bytes = (size_t)b->h_inst[i].a.plane * 9 * elem;
+      cudaMemcpyAsync(b->h_inst[i].buf[b->parity], saved[i], bytes, cudaMemcpyDeviceToDevice, b->stream);
+      off += bytes;
+    }
+    cudaMemcpyAsync(b->d_tctr, &tctr0, sizeof(tctr0), cudaMemcpyHostToDevice, b->stream);
+    cudaStreamSynchronize(b->stream);
+    cudaFree(store);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    st = set_shape(b, best);
+    if (st) return st;
+    if (chosen) *chosen = best;
+    if (ms_per_step) *ms_per_step = best_ms / steps;
+    return LBMP_OK;
+  } catch (...) {
+    return bfail(LBMP_ECUDA, "lbmp_batch_tune: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out) {
+  if (!b || !out) return bfail(LBMP_EINVAL, "NULL argument");
+  out->count = b->count;
+  out->shape_threads = lbmp::kShapes[b->shape].bx;
+  out->shape_nodes_per_thread = lbmp::kShapes[b->shape].npt;
+  out->persistent = lbmp::kShapes[b->shape].persistent;
+  out->total_nodes = b->total_nodes;
+  out->steps = b->steps;
+  out->launches = b->launches;
+  out->device_bytes = b->device_bytes;
+  out->bytes_per_update = 2.0 * 9.0 * (b->p.storage == LBMP_STORE_FP32 ? 4.0 : 2.0) + 8.0;
+  return LBMP_OK;
+}
+
+}  // extern "C"

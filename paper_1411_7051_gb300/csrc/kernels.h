@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "lattice.cuh"
+#include "lbmp.h"
 
 namespace lbmp {
 
@@ -45,6 +46,10 @@ cudaError_t launch_staged(int storage, bool sr, const StepArgs &a, int rows, con
                           unsigned *err, int nsm, cudaStream_t s);
 // Store msg as the calling thread's lbmp_last_error() text.
 void set_last_error(const char *msg);
+
+// Check the parameters of lbmp_create (and normalise J = 0, rho0 = 0 to 1);
+// EINVAL with a message when invalid.  Touches no device.
+lbmp_status validate_params(::lbmp_params *p);
 
 // *tctr += n (one thread).
 cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s);

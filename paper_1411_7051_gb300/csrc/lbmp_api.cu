@@ -286,6 +286,41 @@ bool valid_where(int32_t w) { return w == LBMP_HOST || w == LBMP_DEVICE; }
 
 }  // namespace
 
+lbmp_status lbmp::validate_params(lbmp_params *p) {
+    if (p->J == 0.0) p->J = 1.0;
+    if (p->rho0 == 0.0) p->rho0 = 1.0;
+    if (p->nx < 1 || p->ny < 1) return fail(LBMP_EINVAL, "nx, ny must be >= 1 (got %d x %d)", p->nx, p->ny);
+    if (p->nx > (1 << 30)) return fail(LBMP_EINVAL, "nx must be <= 2^30");
+    if (p->ny > 65535) return fail(LBMP_EINVAL, "ny must be <= 65535");
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(LBMP_EINVAL, "tau must be > 0.5 (got %g)", p->tau);
+    if (!(p->J > 0.0) || !std::isfinite(p->J)) return fail(LBMP_EINVAL, "J must be > 0");
+    if (!std::isfinite(p->Gx) || !std::isfinite(p->Gy)) return fail(LBMP_EINVAL, "G must be finite");
+    if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return fail(LBMP_EINVAL, "rho0 must be > 0");
+    if (p->bc_x != LBMP_BCX_PERIODIC && p->bc_x != LBMP_BCX_PRESSURE)
+      return fail(LBMP_EINVAL, "bc_x must be LBMP_BCX_PERIODIC or LBMP_BCX_PRESSURE");
+    if (p->bc_y != LBMP_BCY_PERIODIC && p->bc_y != LBMP_BCY_WALLS)
+      return fail(LBMP_EINVAL, "bc_y must be LBMP_BCY_PERIODIC or LBMP_BCY_WALLS");
+    if (p->bc_x == LBMP_BCX_PRESSURE) {
+      if (p->nx < 3) return fail(LBMP_EINVAL, "pressure columns need nx >= 3");
+      if (!(p->rho_in > 0.0) || !(p->rho_out > 0.0) || !std::isfinite(p->rho_in) ||
+          !std::isfinite(p->rho_out))
+        return fail(LBMP_EINVAL, "rho_in and rho_out must be finite and > 0");
+    }
+    if (p->bc_y == LBMP_BCY_WALLS && p->ny < 3) return fail(LBMP_EINVAL, "walls need ny >= 3");
+    if (p->forchheimer != 0 && p->forchheimer != 1) return fail(LBMP_EINVAL, "forchheimer must be 0 or 1");
+    if (p->storage != LBMP_STORE_FP32 && p->storage != LBMP_STORE_FP16)
+      return fail(LBMP_EINVAL, "storage must be LBMP_STORE_FP32 or LBMP_STORE_FP16");
+    if (p->fp16_log2_scale < -60 || p->fp16_log2_scale > 60)
+      return fail(LBMP_EINVAL, "fp16_log2_scale must be in [-60, 60]");
+    if (p->kernel != LBMP_KERNEL_AUTO && p->kernel != LBMP_KERNEL_STAGED && p->kernel != LBMP_KERNEL_DIRECT)
+      return fail(LBMP_EINVAL, "kernel must be LBMP_KERNEL_AUTO, _STAGED or _DIRECT");
+    if (p->reserved != 0) return fail(LBMP_EINVAL, "reserved must be 0");
+    if (p->fp16_rounding != LBMP_ROUND_STOCHASTIC && p->fp16_rounding != LBMP_ROUND_NEAREST)
+      return fail(LBMP_EINVAL, "fp16_rounding must be LBMP_ROUND_STOCHASTIC or LBMP_ROUND_NEAREST");
+
+  return LBMP_OK;
+}
+
 extern "C" {
 
 const char *lbmp_last_error(void) { return g_err.c_str(); }
@@ -300,36 +335,8 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     if (!pin || !out) return fail(LBMP_EINVAL, "lbmp_create: NULL argument");
     *out = nullptr;
     lbmp_params p = *pin;
-    if (p.J == 0.0) p.J = 1.0;
-    if (p.rho0 == 0.0) p.rho0 = 1.0;
-    if (p.nx < 1 || p.ny < 1) return fail(LBMP_EINVAL, "nx, ny must be >= 1 (got %d x %d)", p.nx, p.ny);
-    if (p.nx > (1 << 30)) return fail(LBMP_EINVAL, "nx must be <= 2^30");
-    if (p.ny > 65535) return fail(LBMP_EINVAL, "ny must be <= 65535");
-    if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return fail(LBMP_EINVAL, "tau must be > 0.5 (got %g)", p.tau);
-    if (!(p.J > 0.0) || !std::isfinite(p.J)) return fail(LBMP_EINVAL, "J must be > 0");
-    if (!std::isfinite(p.Gx) || !std::isfinite(p.Gy)) return fail(LBMP_EINVAL, "G must be finite");
-    if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0)) return fail(LBMP_EINVAL, "rho0 must be > 0");
-    if (p.bc_x != LBMP_BCX_PERIODIC && p.bc_x != LBMP_BCX_PRESSURE)
-      return fail(LBMP_EINVAL, "bc_x must be LBMP_BCX_PERIODIC or LBMP_BCX_PRESSURE");
-    if (p.bc_y != LBMP_BCY_PERIODIC && p.bc_y != LBMP_BCY_WALLS)
-      return fail(LBMP_EINVAL, "bc_y must be LBMP_BCY_PERIODIC or LBMP_BCY_WALLS");
-    if (p.bc_x == LBMP_BCX_PRESSURE) {
-      if (p.nx < 3) return fail(LBMP_EINVAL, "pressure columns need nx >= 3");
-      if (!(p.rho_in > 0.0) || !(p.rho_out > 0.0) || !std::isfinite(p.rho_in) ||
-          !std::isfinite(p.rho_out))
-        return fail(LBMP_EINVAL, "rho_in and rho_out must be finite and > 0");
-    }
-    if (p.bc_y == LBMP_BCY_WALLS && p.ny < 3) return fail(LBMP_EINVAL, "walls need ny >= 3");
-    if (p.forchheimer != 0 && p.forchheimer != 1) return fail(LBMP_EINVAL, "forchheimer must be 0 or 1");
-    if (p.storage != LBMP_STORE_FP32 && p.storage != LBMP_STORE_FP16)
-      return fail(LBMP_EINVAL, "storage must be LBMP_STORE_FP32 or LBMP_STORE_FP16");
-    if (p.fp16_log2_scale < -60 || p.fp16_log2_scale > 60)
-      return fail(LBMP_EINVAL, "fp16_log2_scale must be in [-60, 60]");
-    if (p.kernel != LBMP_KERNEL_AUTO && p.kernel != LBMP_KERNEL_STAGED && p.kernel != LBMP_KERNEL_DIRECT)
-      return fail(LBMP_EINVAL, "kernel must be LBMP_KERNEL_AUTO, _STAGED or _DIRECT");
-    if (p.reserved != 0) return fail(LBMP_EINVAL, "reserved must be 0");
-    if (p.fp16_rounding != LBMP_ROUND_STOCHASTIC && p.fp16_rounding != LBMP_ROUND_NEAREST)
-      return fail(LBMP_EINVAL, "fp16_rounding must be LBMP_ROUND_STOCHASTIC or LBMP_ROUND_NEAREST");
+    lbmp_status vst = lbmp::validate_params(&p);
+    if (vst) return vst;
 
     lbmp_ctx *c = new (std::nothrow) lbmp_ctx();
     if (!c) return fail(LBMP_ENOMEM, "host allocation of the context");

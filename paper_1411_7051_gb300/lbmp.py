@@ -63,6 +63,17 @@ class Info(ctypes.Structure):
     ]
 
 
+class BatchInfo(ctypes.Structure):
+    """Mirror of ``lbmp_batch_info``."""
+    _fields_ = [
+        ("count", ctypes.c_int32), ("shape_threads", ctypes.c_int32),
+        ("shape_nodes_per_thread", ctypes.c_int32), ("persistent", ctypes.c_int32),
+        ("total_nodes", ctypes.c_int64), ("steps", ctypes.c_int64),
+        ("launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("bytes_per_update", ctypes.c_double),
+    ]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -120,6 +131,26 @@ def load(path: str = LIB_PATH):
     L.lbmp_get_info.argtypes = [_VP, ctypes.POINTER(Info)]
     L.lbmp_permeability_noalloc.restype = st
     L.lbmp_permeability_noalloc.argtypes = [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]
+    I32P = ctypes.POINTER(ctypes.c_int32)
+    L.lbmp_batch_create.restype = st
+    L.lbmp_batch_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, I32P, I32P,
+                                    ctypes.POINTER(_VP)]
+    L.lbmp_batch_destroy.restype = st
+    L.lbmp_batch_destroy.argtypes = [_VP]
+    L.lbmp_batch_set_fields.restype = st
+    L.lbmp_batch_set_fields.argtypes = [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int32]
+    L.lbmp_batch_step.restype = st
+    L.lbmp_batch_step.argtypes = [_VP, ctypes.c_int64]
+    L.lbmp_batch_synchronize.restype = st
+    L.lbmp_batch_synchronize.argtypes = [_VP]
+    L.lbmp_batch_permeability.restype = st
+    L.lbmp_batch_permeability.argtypes = [_VP, _D, _D]
+    L.lbmp_batch_populations.restype = st
+    L.lbmp_batch_populations.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
+    L.lbmp_batch_tune.restype = st
+    L.lbmp_batch_tune.argtypes = [_VP, ctypes.c_int32, I32P, _D]
+    L.lbmp_batch_get_info.restype = st
+    L.lbmp_batch_get_info.argtypes = [_VP, ctypes.POINTER(BatchInfo)]
     _lib = L
     return L
 
@@ -328,3 +359,86 @@ class Sim:
             if r < tol:
                 return r
         raise RuntimeError(f"residual did not reach {tol} in {max_steps} steps")
+
+
+class Batch:
+    """Many lattices advanced together (``lbmp_batch``): ``sizes`` is a list
+    of (nx, ny); the physics of ``cfg`` is shared (its nx, ny are ignored)."""
+
+    def __init__(self, cfg: SimConfig, sizes, stream=None):
+        torch = _torch()
+        L = load()
+        if not torch.cuda.is_available():
+            raise LbmpError(ECUDA, "no CUDA device available")
+        self.cfg = cfg
+        self.sizes = [(int(nx), int(ny)) for nx, ny in sizes]
+        self.count = len(self.sizes)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._params = cfg.to_params(self.stream.cuda_stream)
+        nx = (ctypes.c_int32 * self.count)(*[s[0] for s in self.sizes])
+        ny = (ctypes.c_int32 * self.count)(*[s[1] for s in self.sizes])
+        h = _VP()
+        _check(L.lbmp_batch_create(ctypes.byref(self._params), self.count, nx, ny, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbmp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_fields(self, i: int, eps, k_i, kn):
+        nx, ny = self.sizes[i]
+        helper = Sim.__new__(Sim)
+        pe, we, ke = Sim._in_field(helper, eps, (ny, nx))
+        pk, wk, kk = Sim._in_field(helper, k_i, (ny, nx))
+        pn, wn, kkn = Sim._in_field(helper, kn, (ny, nx))
+        if not (we == wk == wn):
+            raise ValueError("eps, k_i and kn must all be on the host or all on the device")
+        if we == DEVICE:
+            _torch().cuda.current_stream().synchronize()
+        _check(load().lbmp_batch_set_fields(self._h, int(i), pe, pk, pn, we))
+
+    def step(self, n: int = 1):
+        _check(load().lbmp_batch_step(self._h, int(n)))
+
+    def synchronize(self):
+        _check(load().lbmp_batch_synchronize(self._h))
+
+    def permeability(self):
+        kg = np.zeros(self.count)
+        um = np.zeros(self.count)
+        _check(load().lbmp_batch_permeability(self._h, kg.ctypes.data_as(_D),
+                                              um.ctypes.data_as(_D)))
+        return kg, um
+
+    def populations(self, i: int, device: bool = True):
+        nx, ny = self.sizes[i]
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device else "cpu"
+        f = torch.empty((9, ny, nx), dtype=torch.float64, device=dev)
+        _check(load().lbmp_batch_populations(self._h, int(i), ctypes.c_void_p(f.data_ptr()),
+                                             DEVICE if device else HOST))
+        return f
+
+    def tune(self, steps: int = 10):
+        chosen = ctypes.c_int32()
+        ms = ctypes.c_double()
+        _check(load().lbmp_batch_tune(self._h, int(steps), ctypes.byref(chosen), ctypes.byref(ms)))
+        return chosen.value, ms.value
+
+    def info(self) -> BatchInfo:
+        out = BatchInfo()
+        _check(load().lbmp_batch_get_info(self._h, ctypes.byref(out)))
+        return out

@@ -1,0 +1,111 @@
+"""Batched sweeps (lbmp_batch_*): every instance of a batch of uneven sizes
+evolves exactly as the same lattice run alone, per-instance permeabilities
+match, FP16 instances stay within 1e-3 of the oracle, and the autotuner
+leaves the state untouched."""
+import numpy as np
+import pytest
+
+from paper_1411_7051_gb300 import lbmp, media
+from helpers import Case, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(64, 40), (96, 33), (131, 20), (256, 64), (100, 100), (5, 7)]
+
+
+def _media():
+    out = []
+    for j, (nx, ny) in enumerate(SIZES):
+        out.append(media.random_medium(nx, ny, seed=100 + j, p_open=0.1, p_solid=0.05,
+                                       log10_k_range=(-3, 0)))
+    return out
+
+
+def _cfg(storage, rounding=lbmp.ROUND_STOCHASTIC, **kw):
+    base = dict(tau=0.75, bc_x=lbmp.BCX_PRESSURE, bc_y=lbmp.BCY_WALLS, rho_in=1.001,
+                rho_out=0.999, forchheimer=1, storage=storage, fp16_rounding=rounding)
+    base.update(kw)
+    return lbmp.SimConfig(1, 1, **base)
+
+
+def _single(cfg, nx, ny, med):
+    c = lbmp.SimConfig(nx, ny, **{k: v for k, v in cfg.__dict__.items() if k not in ("nx", "ny")})
+    c.kernel = lbmp.KERNEL_DIRECT
+    s = lbmp.Sim(c)
+    s.set_fields(med.eps, med.k_i, med.kn)
+    return s
+
+
+@pytest.mark.parametrize("storage,rounding", [(lbmp.STORE_FP32, lbmp.ROUND_STOCHASTIC),
+                                              (lbmp.STORE_FP16, lbmp.ROUND_NEAREST)])
+def test_batch_instances_match_single_runs(storage, rounding):
+    cfg = _cfg(storage, rounding)
+    meds = _media()
+    with lbmp.Batch(cfg, SIZES) as b:
+        for j, m in enumerate(meds):
+            b.set_fields(j, m.eps, m.k_i, m.kn)
+        b.step(70)   # two graph replays and six single launches
+        kg_b, _ = b.permeability()
+        for j, ((nx, ny), m) in enumerate(zip(SIZES, meds)):
+            s = _single(cfg, nx, ny, m)
+            s.step(70)
+            fb = b.populations(j).cpu().numpy()
+            fs = s.populations().cpu().numpy()
+            np.testing.assert_allclose(fb, fs, rtol=0, atol=1e-12)
+            kg_s, _ = s.permeability()
+            assert kg_b[j] == pytest.approx(kg_s, rel=1e-12, abs=0)
+            s.close()
+
+
+def test_batch_fp16_sr_against_oracle(orc):
+    cfg = _cfg(lbmp.STORE_FP16, lbmp.ROUND_STOCHASTIC, bc_x=lbmp.BCX_PERIODIC, G=(1e-5, 0.0),
+               bc_y=lbmp.BCY_WALLS)
+    sizes = [(64, 33), (48, 24)]
+    meds = [media.channel(64, 33, 0.7, 1e-3, 0.1),
+            media.two_component(48, seed=7, corr_len=6.0, kn=0.5, ny=24, matrix=(0.4, 0.1),
+                                inclusion=(0.8, 1.0))]
+    with lbmp.Batch(cfg, sizes) as b:
+        for j, m in enumerate(meds):
+            b.set_fields(j, m.eps, m.k_i, m.kn)
+        b.step(3000)
+        kg_b, _ = b.permeability()
+    for j, ((nx, ny), m) in enumerate(zip(sizes, meds)):
+        o = oracle_sim(orc, Case(nx, ny, tau=0.75, G=(1e-5, 0.0), walls=True, medium=m))
+        o.step(3000)
+        kg_o, _ = o.permeability()
+        assert abs(kg_b[j] / kg_o - 1) <= 1e-3, (j, kg_b[j], kg_o)
+
+
+def test_batch_tuner_keeps_the_state():
+    cfg = _cfg(lbmp.STORE_FP32)
+    meds = _media()
+    a = lbmp.Batch(cfg, SIZES)
+    b = lbmp.Batch(cfg, SIZES)
+    for j, m in enumerate(meds):
+        a.set_fields(j, m.eps, m.k_i, m.kn)
+        b.set_fields(j, m.eps, m.k_i, m.kn)
+    a.step(10)
+    b.step(10)
+    chosen, ms = a.tune(steps=4)
+    assert 0 <= chosen < 9 and ms > 0
+    info = a.info()
+    assert info.shape_threads * info.shape_nodes_per_thread in (128, 256, 512)
+    a.step(40)
+    b.step(40)
+    for j in range(len(SIZES)):
+        np.testing.assert_allclose(a.populations(j).cpu().numpy(), b.populations(j).cpu().numpy(),
+                                   rtol=0, atol=1e-12)
+    assert a.info().steps == 50
+
+
+def test_batch_state_errors():
+    cfg = _cfg(lbmp.STORE_FP32)
+    with lbmp.Batch(cfg, SIZES[:2]) as b:
+        m = _media()[0]
+        b.set_fields(0, m.eps, m.k_i, m.kn)
+        with pytest.raises(lbmp.LbmpError) as ei:
+            b.step(1)
+        assert ei.value.status == lbmp.ESTATE
+    with pytest.raises(lbmp.LbmpError) as ei:
+        lbmp.Batch(cfg, [(64, 40), (2, 10)])   # pressure columns need nx >= 3
+    assert ei.value.status == lbmp.EINVAL
