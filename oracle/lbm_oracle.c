@@ -458,3 +458,50 @@ void orc_lattice(int *ex, int *ey, double *w) {
     w[i] = ORC_W[i];
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* Gradient of the global permeability by central differences: the      */
+/* definition of the derivative, no adjoint.  For each listed node j,    */
+/*   out[m] = (k_g(theta + h e_j) - k_g(theta - h e_j)) / (2 h),         */
+/* k_g after nsteps steps from rest, theta_j = ln k_i(j) (which = 0) or   */
+/* eps(j) (which = 1), m the position of j in `nodes`.  Each evaluation  */
+/* is a separate lattice; they run in parallel (the loops inside         */
+/* orc_step are then nested regions and run serially).  Returns 0, or   */
+/* -1 when a node index is out of range or memory runs out.              */
+/* ------------------------------------------------------------------ */
+int orc_kg_fd(const orc_params *p, const double *eps, const double *k_i,
+              const double *kn, int64_t nsteps, double h,
+              const int64_t *nodes, int64_t count, int which, double *out) {
+  const int64_t n = (int64_t)p->nx * p->ny;
+  double *kg = (double *)calloc((size_t)(2 * count + 1), sizeof(double));
+  if (!kg) return -1;
+  int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : failed)
+  for (int64_t e = 0; e < 2 * count; ++e) {
+    const int64_t j = nodes[e / 2];
+    const double sign = (e % 2 == 0) ? 1.0 : -1.0;
+    double *pe = (double *)malloc((size_t)n * sizeof(double));
+    double *pk = (double *)malloc((size_t)n * sizeof(double));
+    orc_sim *s = orc_create(p);
+    if (!pe || !pk || !s || j < 0 || j >= n) {
+      failed |= 1;
+    } else {
+      memcpy(pe, eps, (size_t)n * sizeof(double));
+      memcpy(pk, k_i, (size_t)n * sizeof(double));
+      if (which == 0)
+        pk[j] = k_i[j] * exp(sign * h);
+      else
+        pe[j] = eps[j] + sign * h;
+      orc_set_fields(s, pe, pk, kn);
+      orc_step(s, nsteps);
+      kg[e] = orc_permeability(s, NULL);
+    }
+    orc_destroy(s);
+    free(pe);
+    free(pk);
+  }
+  if (!failed)
+    for (int64_t m = 0; m < count; ++m) out[m] = (kg[2 * m] - kg[2 * m + 1]) / (2.0 * h);
+  free(kg);
+  return failed ? -1 : 0;
+}

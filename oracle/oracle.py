@@ -93,6 +93,9 @@ def _load(path: str):
     L.orc_residual.restype = ctypes.c_double
     L.orc_residual.argtypes = [ctypes.c_void_p, _D, _D]
     L.orc_lattice.argtypes = [_I, _I, _D]
+    L.orc_kg_fd.restype = ctypes.c_int
+    L.orc_kg_fd.argtypes = [P, _D, _D, _D, ctypes.c_int64, ctypes.c_double,
+                            ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.c_int, _D]
     return L
 
 
@@ -203,6 +206,27 @@ def set_threads(n: int) -> None:
 
 def max_threads() -> int:
     return int(lib().orc_max_threads())
+
+
+def permeability_gradient_fd(params: Params, eps, k_i, kn, nsteps: int, nodes,
+                             which: str = "logk", h: float = 1e-4) -> np.ndarray:
+    """Central differences of k_g after ``nsteps`` steps from rest with
+    respect to ln k_i (``which="logk"``) or eps (``which="eps"``) of each
+    node in ``nodes`` (flat row-major indices into the [ny][nx] fields).
+    The definition of the derivative applied to the oracle; FP64."""
+    ny, nx = params.ny, params.nx
+    e = np.ascontiguousarray(np.broadcast_to(_vec(eps), (ny, nx)))
+    k = np.ascontiguousarray(np.broadcast_to(_vec(k_i), (ny, nx)))
+    n = np.ascontiguousarray(np.broadcast_to(_vec(kn), (ny, nx)))
+    idx = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64).ravel())
+    out = np.zeros(idx.size)
+    w = {"logk": 0, "eps": 1}[which]
+    rc = lib().orc_kg_fd(ctypes.byref(params), _dp(e), _dp(k), _dp(n), int(nsteps), float(h),
+                         idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), idx.size, w,
+                         _dp(out))
+    if rc != 0:
+        raise ValueError("oracle: finite-difference gradient failed (bad node index or memory)")
+    return out
 
 
 # ---- whole-domain simulation ---------------------------------------------
