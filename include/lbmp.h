@@ -183,6 +183,35 @@ lbmp_status lbmp_set_state(lbmp_ctx *ctx, const void *buf, size_t bytes, int32_t
 /* Sizes, storage and counters of ctx. */
 lbmp_status lbmp_get_info(lbmp_ctx *ctx, lbmp_info *out);
 
+/* Gradient of the global permeability with respect to the medium, by the
+ * discrete adjoint of the time loop.  The objective is
+ *   J(ln k_i, eps) = k_g after nsteps time steps from rest,
+ * k_g as lbmp_permeability defines it (Darcy's law over the whole domain,
+ * Section IV.A) and each step the collide-stream update of Section III
+ * (Eq. 12, equilibrium Eq. 14, forcing Eq. 15, velocity Eq. 16-17 with the
+ * drag of Eq. 2), the plates, periodic edges and pressure columns of this
+ * context.  On return:
+ *   k_g      (host, may be NULL) J, equal to what lbmp_permeability reports
+ *            after lbmp_set_fields + lbmp_step(ctx, nsteps);
+ *   d_logk   [ny][nx] float64, dJ/d ln k_i of every node (k_a = k_i f_c(Kn)
+ *            with Kn held fixed, so also dJ/d ln k_a);
+ *   d_eps    [ny][nx] float64, dJ/d eps of every node, including the
+ *            mean-porosity term of the pressure drop in G_eff;
+ *   where    LBMP_HOST or LBMP_DEVICE for d_logk and d_eps.
+ * Plate rows read 0.  At impermeable (eps = 0) and open (k_a infinite)
+ * nodes the derivatives of the flow part are the one-sided ones of the
+ * branch the step takes there (0 for d_logk).  The forward states are
+ * recomputed from checkpoints taken every `every` steps (0: ceil(sqrt(
+ * nsteps))), holding ceil(nsteps / every) + every + 3 population buffers on
+ * the device; gradients accumulate in FP64, the adjoint populations are
+ * FP32.  The context is left at time level nsteps of a run from rest (its
+ * previous state is replaced).  Needs FP32 storage.  Synchronous.
+ * Errors: EINVAL (NULL pointer, nsteps < 1, every < 0, FP16 storage),
+ * ESTATE (no fields set), ENOMEM, ENAN, ETIMEOUT, ECUDA. */
+lbmp_status lbmp_permeability_gradient(lbmp_ctx *ctx, int64_t nsteps, int64_t every,
+                                       double *k_g, double *d_logk, double *d_eps,
+                                       int32_t where);
+
 /* ---------------------------------------------------------------------
  * Batched sweeps.  `count` lattices of their own sizes (e.g. media
  * realizations x Knudsen numbers) share the physics parameters of p (tau, J,
@@ -191,9 +220,8 @@ lbmp_status lbmp_get_info(lbmp_ctx *ctx, lbmp_info *out);
  * step covers a work list of row segments of all instances, either one block
  * per segment or a persistent grid walking it (CUDA graphs of 32 steps).  Each instance has its own populations, medium
  * and FP16 scale; the arithmetic per node is that of lbmp_step (Section III,
- * Eq. 12-17).  The launch shape (threads per block x nodes per thread) is
- * (threads per block x nodes per thread x grid mode) is chosen by
- * lbmp_batch_tune.
+ * Eq. 12-17).  The launch shape (threads per block x nodes per thread x
+ * grid mode) is chosen by lbmp_batch_tune.
  * --------------------------------------------------------------------- */
 typedef struct lbmp_batch lbmp_batch;
 

@@ -1,6 +1,6 @@
 """Build the CUDA library ``liblbmp.so`` in-tree for sm_103a (GB300).
 
-Two translation units are compiled in parallel with nvcc and linked into a
+The translation units are compiled in parallel with nvcc and linked into a
 shared library with the CUDA runtime linked statically, so the library only
 needs the NVIDIA driver at run time.  No torch headers are involved: the
 library exposes a plain C ABI (``include/lbmp.h``).
@@ -19,8 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbmp.so")
-SOURCES = ["kernels.cu", "lbmp_api.cu", "noalloc.cu", "batch.cu"]
-HEADERS = ["lattice.cuh", "kernels.h", "staged.cuh"]
+SOURCES = ["kernels.cu", "lbmp_api.cu", "noalloc.cu", "batch.cu", "adjoint.cu"]
+HEADERS = ["lattice.cuh", "kernels.h", "staged.cuh", "context.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "-Xptxas", "-O3", "--expt-relaxed-constexpr"]

@@ -1,0 +1,79 @@
+// The library context behind the opaque lbmp_ctx handle (internal to the
+// library: shared by the C ABI and the adjoint translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+
+#include "kernels.h"
+#include "lbmp.h"
+
+struct lbmp_ctx {
+  lbmp_params p{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  int pitch = 0;
+  long long plane = 0;
+  int y_lo = 0, y_hi = 0;   // fluid rows [y_lo, y_hi)
+  size_t elem = 4;
+  void *buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  float2 *med = nullptr;
+  float2 *uprev = nullptr;
+  double *partials = nullptr;
+  int partials_blocks = 0;
+  double *results = nullptr;    // device, kNQ doubles
+  double *h_results = nullptr;  // pinned host, kNQ doubles
+  unsigned *d_flag = nullptr;
+  unsigned long long *d_tctr = nullptr;  // time level for the stochastic rounding
+  unsigned *d_err = nullptr;             // raised by a bounded wait that gave up
+  int nsm = 1;                           // SMs of the device
+  bool staged = true;
+  bool sr = false;
+  bool fields_set = false;
+  int64_t steps = 0;
+  int64_t launches = 0;
+  double scale = 1.0;
+  double eps_mean = 1.0;
+  int64_t fluid_nodes = 0;
+  int64_t device_bytes = 0;
+  int alloc_count = 0;
+  int fault_alloc_at = 0;       // simulated allocation failure (testing)
+  int drop_tile = -1;           // withheld tile of the staged kernel (testing)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+  lbmp::StepArgs args() const {
+    lbmp::StepArgs a;
+    a.nx = p.nx;
+    a.ny = p.ny;
+    a.pitch = pitch;
+    a.y0 = y_lo;
+    a.plane = plane;
+    a.rho0 = (float)p.rho0;
+    a.drho_in = (float)(p.rho_in - p.rho0);
+    a.drho_out = (float)(p.rho_out - p.rho0);
+    a.omega = (float)(1.0 / p.tau);
+    a.one_m_omega = (float)(1.0 - 1.0 / p.tau);
+    a.cforce = (float)(1.0 - 0.5 / p.tau);
+    a.nu = (float)((p.tau - 0.5) / 3.0 / p.J);
+    a.Gx = (float)p.Gx;
+    a.Gy = (float)p.Gy;
+    a.fe_half = (float)(0.5 * 1.75 / std::sqrt(150.0));
+    a.scale = (float)scale;
+    a.inv_scale = (float)(1.0 / scale);
+    a.walls = p.bc_y == LBMP_BCY_WALLS;
+    a.pressure = p.bc_x == LBMP_BCX_PRESSURE;
+    a.forch = p.forchheimer != 0;
+    a.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
+    a.seed_hi = (uint32_t)(p.seed >> 32);
+    a.test_drop_tile = drop_tile;
+    return a;
+  }
+  int rows() const { return y_hi - y_lo; }
+  size_t buf_bytes() const { return (size_t)plane * 9 * elem; }
+};

@@ -129,6 +129,9 @@ def load(path: str = LIB_PATH):
     L.lbmp_set_state.argtypes = [_VP, _VP, ctypes.c_size_t, ctypes.c_int32]
     L.lbmp_get_info.restype = st
     L.lbmp_get_info.argtypes = [_VP, ctypes.POINTER(Info)]
+    L.lbmp_permeability_gradient.restype = st
+    L.lbmp_permeability_gradient.argtypes = [_VP, ctypes.c_int64, ctypes.c_int64, _D, _VP, _VP,
+                                             ctypes.c_int32]
     L.lbmp_permeability_noalloc.restype = st
     L.lbmp_permeability_noalloc.argtypes = [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]
     I32P = ctypes.POINTER(ctypes.c_int32)
@@ -349,6 +352,19 @@ class Sim:
         _check(load().lbmp_get_info(self._h, ctypes.byref(out)))
         return out
 
+    def permeability_gradient(self, nsteps: int, every: int = 0, device: bool = True):
+        """``lbmp_permeability_gradient``: (k_g, dk_g/d ln k_i, dk_g/d eps)
+        after ``nsteps`` steps from rest, by the discrete adjoint with
+        checkpoints every ``every`` steps (0: sqrt(nsteps)).  The gradients
+        are [ny, nx] float64 tensors.  Leaves the lattice at level nsteps."""
+        shape = (self.ny, self.nx)
+        gl, pl, w = self._out_field(shape, device)
+        ge, pe, _ = self._out_field(shape, device)
+        kg = ctypes.c_double()
+        _check(load().lbmp_permeability_gradient(self._h, int(nsteps), int(every),
+                                                 ctypes.byref(kg), pl, pe, w))
+        return kg.value, gl, ge
+
     def run_to_steady(self, tol: float, check_every: int = 100, max_steps: int = 2_000_000):
         """Step until the relative velocity residual over ``check_every``
         steps is below ``tol`` (FP32 storage floors near 1e-7)."""
@@ -359,6 +375,52 @@ class Sim:
             if r < tol:
                 return r
         raise RuntimeError(f"residual did not reach {tol} in {max_steps} steps")
+
+
+_KA_FN = None
+
+
+def _ka_function():
+    """The torch.autograd.Function behind :func:`ka_from_fields` (created on
+    first use so that importing this module does not import torch)."""
+    global _KA_FN
+    if _KA_FN is not None:
+        return _KA_FN
+    torch = _torch()
+
+    class KaFromFields(torch.autograd.Function):
+        """k_g(ln k_i, eps) after a fixed number of steps from rest.  The
+        forward pass runs the time loop and the adjoint in one library call
+        (lbmp_permeability_gradient) when a gradient is needed, else the
+        plain time loop; backward scales the stored gradient fields."""
+
+        @staticmethod
+        def forward(ctx, log_k, eps, sim, kn, nsteps, every):
+            sim.set_fields(eps, torch.exp(log_k.detach()), kn)
+            if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
+                kg, gl, ge = sim.permeability_gradient(nsteps, every, device=True)
+                ctx.save_for_backward(gl.to(log_k.device), ge.to(eps.device))
+            else:
+                sim.step(nsteps)
+                kg, _ = sim.permeability()
+            return torch.tensor(kg, dtype=torch.float64, device=log_k.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            gl, ge = ctx.saved_tensors
+            return grad * gl, grad * ge, None, None, None, None
+
+    _KA_FN = KaFromFields
+    return _KA_FN
+
+
+def ka_from_fields(sim: "Sim", log_k, eps, kn, nsteps: int, every: int = 0):
+    """Global permeability after ``nsteps`` steps from rest as a
+    differentiable function of the [ny, nx] fields ``log_k`` (= ln k_i) and
+    ``eps`` (float64 CUDA tensors); ``kn`` is held fixed.  Returns a 0-d
+    float64 tensor; its backward pass gives dk_g/d ln k_i and dk_g/d eps
+    from the discrete adjoint."""
+    return _ka_function().apply(log_k, eps, sim, kn, nsteps, every)
 
 
 class Batch:
