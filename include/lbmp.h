@@ -203,8 +203,9 @@ lbmp_status lbmp_get_info(lbmp_ctx *ctx, lbmp_info *out);
  * branch the step takes there (0 for d_logk).  The forward states are
  * recomputed from checkpoints taken every `every` steps (0: ceil(sqrt(
  * nsteps))), holding ceil(nsteps / every) + every + 3 population buffers on
- * the device; gradients accumulate in FP64, the adjoint populations are
- * FP32.  The context is left at time level nsteps of a run from rest (its
+ * the device (FP32, like the adjoint populations); each reverse step's
+ * parameter derivatives are summed in FP32 over at most 32 steps, then in
+ * FP64.  The context is left at time level nsteps of a run from rest (its
  * previous state is replaced).  Needs FP32 storage.  Synchronous.
  * Errors: EINVAL (NULL pointer, nsteps < 1, every < 0, FP16 storage),
  * ESTATE (no fields set), ENOMEM, ENAN, ETIMEOUT, ECUDA. */

@@ -1,27 +1,35 @@
 // Discrete adjoint of the time loop (Section III, Eq. 12-17) for the global
-// permeability k_g = nu <u_x> / G_eff of the final time level: gradients
-// with respect to ln k_i and eps of every node.
+// permeability k_g = nu <u_x> / G_eff of the final time level (Darcy's law
+// over the domain, Section IV.A): gradients with respect to ln k_a and eps
+// of every node.
 //
-// Forward state: f^{n+1} = Phi(f^n; theta), Phi = stream o collide, plus the
-// pressure columns f^{n+1}_b = NEEP(f^{n+1}_neighbour; theta) (non-equilibrium
-// extrapolation).  The adjoint Lambda^n = dJ/df^n runs backwards:
-//   1. NEEP adjoint: Lambda^{n+1} of a pressure column is pushed into its
-//      interior neighbour (and into the eps / 1/k_a gradients);
-//   2. reverse streaming: lambda*_i(z) = Lambda^{n+1}_i(z + e_i) (bounce-back
-//      at plates, zero for values a pressure column overwrites);
-//   3. collision transpose: post_i = (1 - 1/tau) f_i + g_i(rho, m; theta), so
-//      Lambda^n_j = (1 - 1/tau) lambda*_j + dG/drho + e_j . dG/dm with
-//      G = sum_i lambda*_i g_i; dG/d(rho, m, eps, kappa) come from forward-mode
-//      dual numbers evaluated on the same formulas as the forward step.
-// States f^n are recomputed segment by segment from checkpoints taken every
-// `every` steps (sqrt(N) by default); gradients accumulate in FP64.
+// Forward: B_{t+1} = C(E(P(B_t))), B the post-collision buffer (B_0 = rest),
+// P the pull (streaming with plates and periodic edges), E the pressure
+// column extrapolation (non-equilibrium, from the adjacent interior node),
+// C the collision of every fluid node; J depends on f^N = E(P(B_N)).
+// Reverse: mu^N = dJ/df^N, then for t = N-1 .. 0
+//   lambda*(z) = mu^{t+1}(z + e_i) for each direction (P transposed: a
+//                plate returns it to the opposite direction of the same
+//                node, a pressure column or the outside returns nothing),
+//   mu^t       = C_t^T lambda* at the state f^t, with E^T folded in: a
+//                column's adjoint is pushed into its interior neighbour by
+//                the thread of that neighbour, which also forms it.
+// C_t^T: post_i = (1 - 1/tau) f_i + g_i(rho, m; eps, k_a) with g_i = f_eq_i /
+// tau + F_i (Eq. 14, 15), so mu_j = (1 - 1/tau) lambda*_j + dG/drho +
+// e_j . dG/dm, G = sum_i lambda*_i g_i.  G is written through the weighted
+// moments L0 = sum w lambda, L1 = sum w lambda e, L2 = sum w lambda e e of
+// lambda* and differentiated by hand, back through the velocity solve of
+// Eq. 16b-17 (with the Forchheimer drag of Eq. 2, the quadratic form).
+// States f^t are recomputed segment by segment from checkpoints taken every
+// `every` steps (sqrt(N) by default).  Each reverse step adds its parameter
+// derivatives to FP32 accumulators, folded into the FP64 gradients every
+// kFold steps (a schedule independent of `every`).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
-#include <vector>
 
 #include "context.h"
 #include "kernels.h"
@@ -30,180 +38,204 @@
 
 namespace lbmp {
 
-// ------------------------------------------------------------ dual numbers
-template <int N>
-struct Dual {
-  float v;
-  float d[N];
-};
-
-template <int N>
-__device__ __forceinline__ Dual<N> dconst(float x) {
-  Dual<N> r;
-  r.v = x;
-#pragma unroll
-  for (int k = 0; k < N; ++k) r.d[k] = 0.0f;
-  return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> dvar(float x, int k0) {
-  Dual<N> r = dconst<N>(x);
-  r.d[k0] = 1.0f;
-  return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator+(const Dual<N> &a, const Dual<N> &b) {
-  Dual<N> r;
-  r.v = a.v + b.v;
-#pragma unroll
-  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k];
-  return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator-(const Dual<N> &a, const Dual<N> &b) {
-  Dual<N> r;
-  r.v = a.v - b.v;
-#pragma unroll
-  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] - b.d[k];
-  return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator-(const Dual<N> &a) {
-  Dual<N> r;
-  r.v = -a.v;
-#pragma unroll
-  for (int k = 0; k < N; ++k) r.d[k] = -a.d[k];
-  return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator*(const Dual<N> &a, const Dual<N> &b) {
-  Dual<N> r;
-  r.v = a.v * b.v;
-#pragma unroll
-  for (int k = 0; k < N; ++k) r.d[k] = fmaf(a.d[k], b.v, a.v * b.d[k]);
-  return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator*(float s, const Dual<N> &a) {
-  Dual<N> r;
-  r.v = s * a.v;
-#pragma unroll
-  for (int k = 0; k < N; ++k) r.d[k] = s * a.d[k];
-  return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator+(float s, const Dual<N> &a) {
-  Dual<N> r = a;
-  r.v = s + a.v;
-  return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator/(const Dual<N> &a, const Dual<N> &b) {
-  Dual<N> r;
-  const float ib = 1.0f / b.v;
-  r.v = a.v * ib;
-#pragma unroll
-  for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
-  return r;
-}
-// sqrt with the zero subgradient at 0
-template <int N>
-__device__ __forceinline__ Dual<N> dsqrt(const Dual<N> &a) {
-  Dual<N> r;
-  r.v = sqrtf(a.v);
-  const float g = (r.v > 0.0f) ? 0.5f / r.v : 0.0f;
-#pragma unroll
-  for (int k = 0; k < N; ++k) r.d[k] = g * a.d[k];
-  return r;
-}
-
-// Velocity (Eq. 17 or the quadratic form with Eq. 2) and force of a node of
-// porosity eps > 0 and kappa = 1/k_a, from rho and the momentum m (sum of
-// populations times e_i), all as duals.
-template <int N>
-struct DVel {
-  Dual<N> ux, uy, Fx, Fy;
-};
-template <int N>
-__device__ __forceinline__ DVel<N> dvelocity(const Dual<N> &rho, const Dual<N> &mx,
-                                             const Dual<N> &my, const Dual<N> &eps,
-                                             const Dual<N> &kap, const StepArgs &a) {
-  const Dual<N> eGx = a.Gx * eps, eGy = a.Gy * eps;
-  const Dual<N> vx = mx / rho + 0.5f * eGx;
-  const Dual<N> vy = my / rho + 0.5f * eGy;
-  const Dual<N> darcy = a.nu * (eps * kap);
-  const Dual<N> c0 = 0.5f + 0.25f * darcy;
-  Dual<N> den, drag;
-  if (a.forch) {
-    const Dual<N> c1 = a.fe_half * dsqrt(kap / eps);
-    const Dual<N> vmag = dsqrt(vx * vx + vy * vy);
-    den = c0 + dsqrt(c0 * c0 + c1 * vmag);
-    drag = darcy + 2.0f * (c1 * (vmag / den));
-  } else {
-    den = 2.0f * c0;
-    drag = darcy;
-  }
-  DVel<N> r;
-  r.ux = vx / den;
-  r.uy = vy / den;
-  r.Fx = eGx - drag * r.ux;
-  r.Fy = eGy - drag * r.uy;
-  return r;
-}
-
-// Porous equilibrium (Eq. 14) of direction i, physical units.
-template <int N>
-__device__ __forceinline__ Dual<N> dfeq(int i, const Dual<N> &rho, const Dual<N> &ux,
-                                        const Dual<N> &uy, const Dual<N> &ieps) {
-  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  const float w = (i == 0) ? kW0 : (i <= 4 ? kW1 : kW2);
-  const Dual<N> eu = (float)ex[i] * ux + (float)ey[i] * uy;
-  const Dual<N> uu = ux * ux + uy * uy;
-  const Dual<N> br = 1.0f + 3.0f * eu + (4.5f * (eu * eu) - 1.5f * uu) * ieps;
-  return w * (rho * br);
-}
-
-// G = sum_i lam_i (omega feq_i + F_i) of a node with eps > 0 (Eq. 14, 15).
-template <int N>
-__device__ __forceinline__ Dual<N> dGamma(const float lam[9], const Dual<N> &rho,
-                                          const Dual<N> &mx, const Dual<N> &my,
-                                          const Dual<N> &eps, const Dual<N> &kap,
-                                          const StepArgs &a) {
-  const DVel<N> v = dvelocity(rho, mx, my, eps, kap, a);
-  const Dual<N> ieps = dconst<N>(1.0f) / eps;
-  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  const Dual<N> uF = v.ux * v.Fx + v.uy * v.Fy;
-  Dual<N> G = dconst<N>(0.0f);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const float w = (i == 0) ? kW0 : (i <= 4 ? kW1 : kW2);
-    const Dual<N> eu = (float)ex[i] * v.ux + (float)ey[i] * v.uy;
-    const Dual<N> eF = (float)ex[i] * v.Fx + (float)ey[i] * v.Fy;
-    const Dual<N> Fi = (w * a.cforce) * (rho * (3.0f * eF + (9.0f * (eu * eF) - 3.0f * uF) * ieps));
-    const Dual<N> gi = a.omega * dfeq(i, rho, v.ux, v.uy, ieps) + Fi;
-    G = G + lam[i] * gi;
-  }
-  return G;
-}
-
 struct AdjArgs {
   StepArgs a;            // forward parameters (FP32 storage, scale 1)
-  float *lam_in;         // Lambda^{n+1}, [9][ny][pitch]
-  float *lam_out;        // Lambda^n
-  const float *fin;      // forward buffer whose pull is f^n (or f^{n+1} for NEEP)
+  const float *lam_in;   // mu^{t+1}, [9][ny][pitch] (pressure columns unused)
+  float *lam_out;        // mu^t
+  const float *fin;      // forward buffer whose pull gives f^t
   const float2 *med;     // (eps, 1/k_a)
-  double *g_eps;         // [ny][pitch] accumulated dJ/deps
-  double *g_kap;         // [ny][pitch] accumulated dJ/dkappa
-  double coef;           // nu / (G_eff * fluid nodes) for the objective seed
+  float2 *acc;           // [ny][pitch] (dJ/d eps, dJ/d ln k_a) of the last few steps, FP32
+  double *g_eps;         // [ny][pitch] dJ/d eps, FP64 (acc folded in every kFold steps)
+  double *g_lk;          // [ny][pitch] dJ/d ln k_a, FP64
+  float coef;            // dJ/du_x of one node: nu / (G_eff * fluid nodes)
 };
+
+constexpr int kAdjBX = 128;
+constexpr int kFold = 32;  // reverse steps summed in FP32 before the FP64 fold
+
+// Weighted moments of an adjoint population vector.
+struct LamMom {
+  float L0, Lx, Ly, Lxx, Lxy, Lyy;
+};
+__device__ __forceinline__ LamMom lam_moments(const float l[9]) {
+  const float s1 = l[1] + l[3], s2 = l[2] + l[4];
+  const float a57 = l[5] + l[7], a68 = l[6] + l[8];
+  const float d57 = l[5] - l[7], d86 = l[8] - l[6];
+  LamMom M;
+  M.L0 = kW0 * l[0] + kW1 * (s1 + s2) + kW2 * (a57 + a68);
+  M.Lx = kW1 * (l[1] - l[3]) + kW2 * (d57 + d86);
+  M.Ly = kW1 * (l[2] - l[4]) + kW2 * (d57 - d86);
+  M.Lxx = kW1 * s1 + kW2 * (a57 + a68);
+  M.Lyy = kW1 * s2 + kW2 * (a57 + a68);
+  M.Lxy = kW2 * (a57 - a68);
+  return M;
+}
+
+// Velocity solve of a node with eps > 0, kept for its adjoint:
+// v = m / rho + eps G / 2, u = v / den, F = eps G - drag u, with
+// den = c0 + s, s = sqrt(c0^2 + c1 |v|), drag = eps nu / k_a + 2 c1 |v| / den
+// (Forchheimer), or den = 2 c0, drag = eps nu / k_a (Darcy only);
+// c0 = 1/2 + eps nu / (4 k_a), c1 = (eps F_eps / 2) / sqrt(k_a).
+struct Vel {
+  float vx, vy, vmag, c0, c1, s, den, id, drag, ux, uy, Fx, Fy;  // id = 1 / den
+};
+__device__ __forceinline__ Vel vel_forward(float rho, float mx, float my, float eps, float kap,
+                                           const StepArgs &a) {
+  Vel V;
+  const float ir = rcp_approx(rho);
+  V.vx = fmaf(mx, ir, 0.5f * eps * a.Gx);
+  V.vy = fmaf(my, ir, 0.5f * eps * a.Gy);
+  const float darcy = a.nu * eps * kap;
+  V.c0 = fmaf(0.25f, darcy, 0.5f);
+  if (a.forch) {
+    V.c1 = a.fe_half * sqrt_approx(kap * rcp_approx(eps));
+    V.vmag = sqrt_approx(fmaf(V.vx, V.vx, V.vy * V.vy));
+    V.s = sqrt_approx(fmaf(V.c0, V.c0, V.c1 * V.vmag));
+    V.den = V.c0 + V.s;
+    V.id = rcp_approx(V.den);
+    V.drag = fmaf(2.0f * V.c1, V.vmag * V.id, darcy);
+  } else {
+    V.c1 = 0.0f;
+    V.vmag = 0.0f;
+    V.s = 0.0f;
+    V.den = 2.0f * V.c0;
+    V.id = rcp_approx(V.den);
+    V.drag = darcy;
+  }
+  V.ux = V.vx * V.id;
+  V.uy = V.vy * V.id;
+  V.Fx = eps * a.Gx - V.drag * V.ux;
+  V.Fy = eps * a.Gy - V.drag * V.uy;
+  return V;
+}
+
+// Sensitivities of a node: d/drho and d/dm of its post-stream moments, and
+// the parameter derivatives d/d eps and d/d ln k_a.
+struct Bar {
+  float rho, mx, my, eps, lk;
+};
+
+// Reverse of vel_forward: adds to b the derivatives of ub . u + Fb . F.
+__device__ __forceinline__ void vel_adjoint(const Vel &V, float rho, float mx, float my,
+                                            float eps, float kap, float ubx, float uby, float Fbx,
+                                            float Fby, const StepArgs &a, Bar &b) {
+  // F = eps G - drag u
+  ubx -= V.drag * Fbx;
+  uby -= V.drag * Fby;
+  const float dragb = -(Fbx * V.ux + Fby * V.uy);
+  b.eps += Fbx * a.Gx + Fby * a.Gy;
+  // u = v / den
+  const float id = V.id;
+  float vbx = ubx * id, vby = uby * id;
+  float denb = -(ubx * V.ux + uby * V.uy) * id;
+  const float darcy = a.nu * eps * kap;
+  float darcyb = dragb, c0b;
+  if (a.forch) {
+    // drag = darcy + 2 c1 |v| / den
+    float c1b = 2.0f * dragb * V.vmag * id;
+    float vmagb = 2.0f * dragb * V.c1 * id;
+    denb -= 2.0f * dragb * V.c1 * V.vmag * id * id;
+    // den = c0 + s, s = sqrt(c0^2 + c1 |v|) >= c0 >= 1/2
+    const float is = rcp_approx(V.s);
+    c0b = denb * (1.0f + V.c0 * is);
+    c1b += 0.5f * denb * V.vmag * is;
+    vmagb += 0.5f * denb * V.c1 * is;
+    // |v|: at v = 0 the terms it enters vanish with u, so its derivative is
+    // not needed there
+    if (V.vmag > 0.0f) {
+      const float iv = rcp_approx(V.vmag);
+      vbx += vmagb * V.vx * iv;
+      vby += vmagb * V.vy * iv;
+    }
+    // c1 = fe_half sqrt(kap / eps): dc1/d ln k_a = -c1 / 2, dc1/d eps = -c1 / (2 eps)
+    b.lk -= 0.5f * V.c1 * c1b;
+    b.eps -= 0.5f * V.c1 * c1b * rcp_approx(eps);
+  } else {
+    c0b = 2.0f * denb;
+  }
+  darcyb += 0.25f * c0b;
+  // darcy = nu eps kap: d/d ln k_a = -darcy, d/d eps = nu kap
+  b.lk -= darcy * darcyb;
+  b.eps += a.nu * kap * darcyb;
+  // v = m / rho + eps G / 2
+  const float ir = rcp_approx(rho);
+  b.mx += vbx * ir;
+  b.my += vby * ir;
+  b.rho -= (vbx * mx + vby * my) * ir * ir;
+  b.eps += 0.5f * (vbx * a.Gx + vby * a.Gy);
+}
+
+// Adds to b the derivatives of G = sum_i lam_i g_i(rho, m; eps, k_a) of one
+// node.  sum_i lam_i f_eq_i = rho [L0 + 3 u.L1 + (9/2 u.L2.u - 3/2 u^2 L0) /
+// eps] (Eq. 14) and sum_i lam_i F_i = (1 - 1/2tau) rho [3 F.L1 + (9 u.L2.F -
+// 3 (u.F) L0) / eps] (Eq. 15); eps = 0 keeps f_eq = w rho, u = 0 and
+// F = -2 m / rho.
+__device__ __forceinline__ void collide_adjoint(const float lam[9], float rho, float mx, float my,
+                                                float eps, float kap, const StepArgs &a, Bar &b) {
+  const LamMom M = lam_moments(lam);
+  const float om = a.omega, cf = a.cforce;
+  if (!(eps > 0.0f)) {
+    b.rho += om * M.L0;
+    b.mx -= 6.0f * cf * M.Lx;
+    b.my -= 6.0f * cf * M.Ly;
+    return;
+  }
+  const Vel V = vel_forward(rho, mx, my, eps, kap, a);
+  const float ie = rcp_approx(eps);
+  const float ux = V.ux, uy = V.uy, Fx = V.Fx, Fy = V.Fy;
+  const float L2ux = M.Lxx * ux + M.Lxy * uy, L2uy = M.Lxy * ux + M.Lyy * uy;
+  const float L2Fx = M.Lxx * Fx + M.Lxy * Fy, L2Fy = M.Lxy * Fx + M.Lyy * Fy;
+  const float qe = 4.5f * (ux * L2ux + uy * L2uy) - 1.5f * (ux * ux + uy * uy) * M.L0;
+  const float qf = 9.0f * (ux * L2Fx + uy * L2Fy) - 3.0f * (ux * Fx + uy * Fy) * M.L0;
+  const float Seq = M.L0 + 3.0f * (ux * M.Lx + uy * M.Ly) + qe * ie;
+  const float SF = 3.0f * (Fx * M.Lx + Fy * M.Ly) + qf * ie;
+  b.rho += om * Seq + cf * SF;
+  // dSeq/du = dSF/dF
+  const float ax = 3.0f * M.Lx + (9.0f * L2ux - 3.0f * ux * M.L0) * ie;
+  const float ay = 3.0f * M.Ly + (9.0f * L2uy - 3.0f * uy * M.L0) * ie;
+  const float ubx = rho * (om * ax + cf * (9.0f * L2Fx - 3.0f * Fx * M.L0) * ie);
+  const float uby = rho * (om * ay + cf * (9.0f * L2Fy - 3.0f * Fy * M.L0) * ie);
+  b.eps -= rho * (om * qe + cf * qf) * ie * ie;
+  vel_adjoint(V, rho, mx, my, eps, kap, ubx, uby, rho * cf * ax, rho * cf * ay, a, b);
+}
+
+// Pressure column b next to interior node n: f_b = f_n + f_eq(rho_b, u_n;
+// eps_b) - f_eq(rho_n, u_n; eps_n).  Adds to bn the derivatives of
+// sum_i lb_i f_b,i with respect to n's moments and parameters (the identity
+// part, lb itself, is added by the caller) and to eb the one of eps_b.
+__device__ __forceinline__ void neep_adjoint(const float lb[9], float rho_n, float mx, float my,
+                                             float eps_n, float kap_n, float eps_b, float rho_b,
+                                             const StepArgs &a, Bar &bn, float &eb) {
+  const LamMom M = lam_moments(lb);
+  if (!(eps_n > 0.0f)) {  // u_n = 0: f_b = f_n + w (rho_b - rho_n)
+    bn.rho -= M.L0;
+    return;
+  }
+  const Vel V = vel_forward(rho_n, mx, my, eps_n, kap_n, a);
+  const float ux = V.ux, uy = V.uy;
+  const float L2ux = M.Lxx * ux + M.Lxy * uy, L2uy = M.Lxy * ux + M.Lyy * uy;
+  const float q = 4.5f * (ux * L2ux + uy * L2uy) - 1.5f * (ux * ux + uy * uy) * M.L0;
+  const float cx = 3.0f * M.Lx, cy = 3.0f * M.Ly;
+  const float qx = 9.0f * L2ux - 3.0f * ux * M.L0, qy = 9.0f * L2uy - 3.0f * uy * M.L0;
+  const float ien = rcp_approx(eps_n);
+  bn.rho -= M.L0 + (ux * cx + uy * cy) + q * ien;
+  float ubx = -rho_n * (cx + qx * ien), uby = -rho_n * (cy + qy * ien);
+  bn.eps += rho_n * q * ien * ien;
+  if (eps_b > 0.0f) {
+    const float ieb = rcp_approx(eps_b);
+    ubx += rho_b * (cx + qx * ieb);
+    uby += rho_b * (cy + qy * ieb);
+    eb -= rho_b * q * ieb * ieb;
+  }
+  vel_adjoint(V, rho_n, mx, my, eps_n, kap_n, ubx, uby, 0.0f, 0.0f, a, bn);
+}
 
 __device__ __forceinline__ float lam_at(const AdjArgs &A, int i, int x, int y) {
   return A.lam_in[i * A.a.plane + (long long)y * A.a.pitch + x];
 }
 
-// Reverse streaming for node (x, y): the adjoint of its post-collision values.
+// Reverse streaming for node (x, y): the adjoint of its post-collision
+// values, read where each of them streams to.
 __device__ __forceinline__ void reverse_pull(const AdjArgs &A, int x, int y, float lp[9]) {
   const StepArgs &a = A.a;
   const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -219,26 +251,16 @@ __device__ __forceinline__ void reverse_pull(const AdjArgs &A, int x, int y, flo
       lp[i] = col ? 0.0f : lam_at(A, opp[i], x, y);  // bounced back into the same node
       continue;
     }
-    yd = (yd + a.ny) % a.ny;
+    yd = (yd < 0) ? yd + a.ny : (yd >= a.ny ? yd - a.ny : yd);
     if (a.pressure) {
       if (xd <= 0 || xd >= a.nx - 1) {  // lost at the edge or received by a pressure column
         lp[i] = 0.0f;
         continue;
       }
     } else {
-      xd = (xd + a.nx) % a.nx;
+      xd = (xd < 0) ? xd + a.nx : (xd >= a.nx ? xd - a.nx : xd);
     }
     lp[i] = lam_at(A, i, xd, yd);
-  }
-}
-
-// Forward post-stream state of node (x, y) from buffer fin (pull + pressure
-// columns), deviations f_i - w_i rho0.
-__device__ __forceinline__ void forward_state(const AdjArgs &A, int x, int y, float d[9]) {
-  pull_node<StoreF32>(A.fin, A.a, x, y, d);
-  if (A.a.pressure && (x == 0 || x == A.a.nx - 1)) {
-    const float2 m = A.med[(long long)y * A.a.pitch + x];
-    pressure_node<StoreF32>(A.fin, A.med, A.a, x, y, m.x, d);
   }
 }
 
@@ -250,158 +272,129 @@ __device__ __forceinline__ void moments(const float d[9], float rho0, float &rho
   my = (d[2] - d[4]) + ((d[5] - d[7]) + (d[6] - d[8]));
 }
 
-// One reverse step for every fluid node: Lambda^n from Lambda^{n+1}, f^n.
-__global__ void __launch_bounds__(128) adjoint_step_kernel(const AdjArgs A) {
+// Adjoint of the pressure column beside interior node (x, y), formed and
+// pushed into the node by the node's own thread: the column's adjoint lb =
+// (1 - 1/tau) lambda*_b + its collision adjoint (SEED: the objective's
+// dJ/df_b instead), then E^T.  Adds lb to mu and the node's moment and
+// parameter sensitivities to bn; writes the column's parameter gradients.
+template <bool SEED>
+__device__ __forceinline__ void column_adjoint(const AdjArgs &A, int x, int y, float rho,
+                                               float mx, float my, float2 mn, float mu[9],
+                                               Bar &bn) {
   const StepArgs &a = A.a;
-  const int y = a.y0 + blockIdx.y;
-  const int x = blockIdx.x * 128 + threadIdx.x;
-  if (x >= a.nx) return;
-  float lp[9], d[9];
-  reverse_pull(A, x, y, lp);
-  forward_state(A, x, y, d);
-  float rho, mx, my;
-  moments(d, a.rho0, rho, mx, my);
-  const long long j = (long long)y * a.pitch + x;
-  const float2 m = A.med[j];
   const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  float ar, amx, amy;
-  if (m.x > 0.0f) {
-    const Dual<5> G = dGamma<5>(lp, dvar<5>(rho, 0), dvar<5>(mx, 1), dvar<5>(my, 2),
-                                dvar<5>(m.x, 3), dvar<5>(m.y, 4), a);
-    ar = G.d[0];
-    amx = G.d[1];
-    amy = G.d[2];
-    A.g_eps[j] += (double)G.d[3];
-    A.g_kap[j] += (double)G.d[4];
-  } else {
-    // impermeable node: g_i = omega w_i rho - 6 (1 - 1/2tau) w_i e_i . m
-    float sw = 0.0f, swx = 0.0f, swy = 0.0f;
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const int xn = side ? a.nx - 2 : 1;
+    if (x != xn) continue;
+    const int xb = side ? a.nx - 1 : 0;
+    const long long jb = (long long)y * a.pitch + xb;
+    const float2 mb = A.med[jb];
+    float fb[9];
+    pressure_node<StoreF32>(A.fin, A.med, a, xb, y, mb.x, fb);
+    float rb, mbx, mby;
+    moments(fb, a.rho0, rb, mbx, mby);
+    Bar bb = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float lb[9];
+    if (SEED) {
+      if (mb.x > 0.0f) {
+        const Vel V = vel_forward(rb, mbx, mby, mb.x, mb.y, a);
+        vel_adjoint(V, rb, mbx, mby, mb.x, mb.y, A.coef, 0.0f, 0.0f, 0.0f, a, bb);
+      }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const float w = (i == 0) ? kW0 : (i <= 4 ? kW1 : kW2);
-      sw += w * lp[i];
-      swx += w * lp[i] * ex[i];
-      swy += w * lp[i] * ey[i];
+      for (int i = 0; i < 9; ++i) lb[i] = bb.rho + ex[i] * bb.mx + ey[i] * bb.my;
+    } else {
+      float lpb[9];
+      reverse_pull(A, xb, y, lpb);
+      collide_adjoint(lpb, rb, mbx, mby, mb.x, mb.y, a, bb);
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        lb[i] = fmaf(a.one_m_omega, lpb[i], bb.rho + ex[i] * bb.mx + ey[i] * bb.my);
     }
-    ar = a.omega * sw;
-    amx = -6.0f * a.cforce * swx;
-    amy = -6.0f * a.cforce * swy;
+    float eb = 0.0f;
+    const float rho_b = a.rho0 + (side ? a.drho_out : a.drho_in);
+    neep_adjoint(lb, rho, mx, my, mn.x, mn.y, mb.x, rho_b, a, bn, eb);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i] += lb[i];
+    const float2 g = A.acc[jb];  // only this thread touches the column node
+    A.acc[jb] = make_float2(g.x + (bb.eps + eb), g.y + bb.lk);
   }
-  const float o1 = a.one_m_omega;
+}
+
+// One reverse step over the fluid rows: mu^t from mu^{t+1} and f^t.
+// SEED: the objective instead, mu^N = dJ/df^N.  Pressure-column threads
+// return at once (their neighbours handle them).
+template <bool SEED>
+__global__ void __launch_bounds__(kAdjBX, 8) adjoint_step_kernel(const AdjArgs A) {
+  const StepArgs &a = A.a;
+  const int y = a.y0 + blockIdx.y;
+  const int x = blockIdx.x * kAdjBX + threadIdx.x;
+  if (x >= a.nx) return;
+  if (a.pressure && (x == 0 || x == a.nx - 1)) return;
+  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const long long j = (long long)y * a.pitch + x;
+  // the accumulators are read up front so that their latency overlaps the
+  // population loads
+  const float2 g0 = A.acc[j];
+  const float2 m = __ldg(A.med + j);
+  float d[9], mu[9];
+  pull_node<StoreF32>(A.fin, a, x, y, d);
+  float rho, mx, my;
+  moments(d, a.rho0, rho, mx, my);
+  Bar b = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (SEED) {
+    if (m.x > 0.0f) {
+      const Vel V = vel_forward(rho, mx, my, m.x, m.y, a);
+      vel_adjoint(V, rho, mx, my, m.x, m.y, A.coef, 0.0f, 0.0f, 0.0f, a, b);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i] = 0.0f;
+  } else {
+    float lp[9];
+    reverse_pull(A, x, y, lp);
+    collide_adjoint(lp, rho, mx, my, m.x, m.y, a, b);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i] = a.one_m_omega * lp[i];
+  }
+  if (a.pressure && (x == 1 || x == a.nx - 2)) column_adjoint<SEED>(A, x, y, rho, mx, my, m, mu, b);
 #pragma unroll
   for (int i = 0; i < 9; ++i)
-    A.lam_out[i * a.plane + j] = fmaf(o1, lp[i], ar + ex[i] * amx + ey[i] * amy);
+    A.lam_out[i * a.plane + j] = mu[i] + b.rho + ex[i] * b.mx + ey[i] * b.my;
+  A.acc[j] = make_float2(g0.x + b.eps, g0.y + b.lk);
 }
 
-// Pressure columns: push Lambda of column 0 / nx-1 into columns 1 / nx-2
-// (in place in lam_in) and into the parameter gradients.  fin is the buffer
-// whose pull gives the post-stream state at the same time level.
-__global__ void adjoint_neep_kernel(const AdjArgs A) {
-  const StepArgs &a = A.a;
-  const int y = a.y0 + blockIdx.x * blockDim.x + threadIdx.x;
-  const int y_end = a.walls ? a.ny - 1 : a.ny;
-  if (y >= y_end) return;
-  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  for (int side = 0; side < 2; ++side) {
-    const int xb = side ? a.nx - 1 : 0;
-    const int xn = side ? a.nx - 2 : 1;
-    const long long jb = (long long)y * a.pitch + xb, jn = (long long)y * a.pitch + xn;
-    float lb[9], d[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) lb[i] = A.lam_in[i * a.plane + jb];
-    pull_node<StoreF32>(A.fin, a, xn, y, d);
-    float rho, mx, my;
-    moments(d, a.rho0, rho, mx, my);
-    const float2 mn = A.med[jn], mb = A.med[jb];
-    const float rho_b = a.rho0 + (side ? a.drho_out : a.drho_in);
-    float ar = 0.0f, amx = 0.0f, amy = 0.0f;
-    if (mn.x > 0.0f) {
-      // Psi = sum_i lb_i (feq_i(rho_b, u_n; eps_b) - feq_i(rho_n, u_n; eps_n))
-      const Dual<6> R = dvar<6>(rho, 0), MX = dvar<6>(mx, 1), MY = dvar<6>(my, 2);
-      const Dual<6> EN = dvar<6>(mn.x, 3), KN = dvar<6>(mn.y, 4), EB = dvar<6>(mb.x, 5);
-      const DVel<6> v = dvelocity(R, MX, MY, EN, KN, a);
-      const Dual<6> ien = dconst<6>(1.0f) / EN;
-      Dual<6> P = dconst<6>(0.0f);
-      if (mb.x > 0.0f) {
-        const Dual<6> ieb = dconst<6>(1.0f) / EB;
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          P = P + lb[i] * (dfeq(i, dconst<6>(rho_b), v.ux, v.uy, ieb) - dfeq(i, R, v.ux, v.uy, ien));
-      } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const float w = (i == 0) ? kW0 : (i <= 4 ? kW1 : kW2);
-          P = P + lb[i] * (dconst<6>(w * rho_b) - dfeq(i, R, v.ux, v.uy, ien));
-        }
-      }
-      ar = P.d[0];
-      amx = P.d[1];
-      amy = P.d[2];
-      A.g_eps[jn] += (double)P.d[3];
-      A.g_kap[jn] += (double)P.d[4];
-      A.g_eps[jb] += (double)P.d[5];
-    } else {
-      // impermeable neighbour: u_n = 0, f_b = f_n + w (rho_b - rho_n)
-      float sw = 0.0f;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) sw += ((i == 0) ? kW0 : (i <= 4 ? kW1 : kW2)) * lb[i];
-      ar = -sw;
-    }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) A.lam_in[i * a.plane + jn] += lb[i] + ar + ex[i] * amx + ey[i] * amy;
-  }
-}
-
-// Objective seed at the final level: Lambda^N = coef * du_x/df, gradients
-// coef * du_x/d(eps, kappa).
-__global__ void __launch_bounds__(128) adjoint_seed_kernel(const AdjArgs A) {
+// Folds the FP32 accumulators of the fluid rows into the FP64 gradients
+// and clears them.
+__global__ void __launch_bounds__(kAdjBX) adjoint_fold_kernel(const AdjArgs A) {
   const StepArgs &a = A.a;
   const int y = a.y0 + blockIdx.y;
-  const int x = blockIdx.x * 128 + threadIdx.x;
+  const int x = blockIdx.x * kAdjBX + threadIdx.x;
   if (x >= a.nx) return;
-  float d[9];
-  forward_state(A, x, y, d);
-  float rho, mx, my;
-  moments(d, a.rho0, rho, mx, my);
   const long long j = (long long)y * a.pitch + x;
-  const float2 m = A.med[j];
-  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  float cr = 0.0f, cx = 0.0f, cy = 0.0f;
-  if (m.x > 0.0f) {
-    const DVel<5> v = dvelocity(dvar<5>(rho, 0), dvar<5>(mx, 1), dvar<5>(my, 2),
-                                dvar<5>(m.x, 3), dvar<5>(m.y, 4), a);
-    const float c = (float)A.coef;
-    cr = c * v.ux.d[0];
-    cx = c * v.ux.d[1];
-    cy = c * v.ux.d[2];
-    A.g_eps[j] += A.coef * (double)v.ux.d[3];
-    A.g_kap[j] += A.coef * (double)v.ux.d[4];
-  }
-#pragma unroll
-  for (int i = 0; i < 9; ++i) A.lam_out[i * a.plane + j] = cr + ex[i] * cx + ey[i] * cy;
+  const float2 g = A.acc[j];
+  A.g_eps[j] += (double)g.x;
+  A.g_lk[j] += (double)g.y;
+  A.acc[j] = make_float2(0.0f, 0.0f);
 }
 
-// dJ/dln k_i = -kappa dJ/dkappa, dJ/deps (+ the mean-porosity term of the
-// pressure drop), into [ny][nx] float64; plate rows read 0.
+// dJ/d ln k_a and dJ/d eps (+ the mean-porosity term of the pressure drop)
+// into [ny][nx] float64; plate rows read 0.
 __global__ void adjoint_assemble_kernel(const AdjArgs A, double eps_term, double *out_logk,
                                         double *out_eps) {
   const StepArgs &a = A.a;
   const int y = blockIdx.y;
-  const int x = blockIdx.x * 128 + threadIdx.x;
+  const int x = blockIdx.x * kAdjBX + threadIdx.x;
   if (x >= a.nx) return;
   const long long o = (long long)y * a.nx + x;
-  const bool wall = a.walls && (y == 0 || y == a.ny - 1);
-  if (wall) {
+  if (a.walls && (y == 0 || y == a.ny - 1)) {
     out_logk[o] = 0.0;
     out_eps[o] = 0.0;
     return;
   }
   const long long j = (long long)y * a.pitch + x;
-  const float2 m = A.med[j];
-  out_logk[o] = -(double)m.y * A.g_kap[j];
+  out_logk[o] = A.g_lk[j];
   out_eps[o] = A.g_eps[j] + eps_term;
 }
 
@@ -478,12 +471,14 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
     ACK(cudaMalloc(&ck.p, state * (size_t)nseg));
     ACK(cudaMalloc(&seg.p, state * (size_t)(every + 1)));
     ACK(cudaMalloc(&lam.p, state * 2));
-    ACK(cudaMalloc(&grad.p, field * 2));
+    const size_t accb = (size_t)c->plane * sizeof(float2);
+    ACK(cudaMalloc(&grad.p, field * 2 + accb));
     ACK(cudaMemsetAsync(lam.p, 0, state * 2, s));
-    ACK(cudaMemsetAsync(grad.p, 0, field * 2, s));
+    ACK(cudaMemsetAsync(grad.p, 0, field * 2 + accb, s));
     char *ckp = (char *)ck.p, *segp = (char *)seg.p;
     float *lam0 = (float *)lam.p, *lam1 = (float *)((char *)lam.p + state);
-    double *g_eps = (double *)grad.p, *g_kap = (double *)((char *)grad.p + field);
+    double *g_eps = (double *)grad.p, *g_lk = (double *)((char *)grad.p + field);
+    float2 *acc = (float2 *)((char *)grad.p + 2 * field);
 
     // forward pass from rest in the context's own buffers, checkpointing
     // the first level of every segment
@@ -518,19 +513,20 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
     A.a = a;
     A.med = c->med;
     A.g_eps = g_eps;
-    A.g_kap = g_kap;
-    A.coef = nu / (geff * nf);
+    A.g_lk = g_lk;
+    A.acc = acc;
+    A.coef = (float)(nu / (geff * nf));
     // seed: Lambda^N = dJ/df^N
-    const dim3 blk(128), grd((a.nx + 127) / 128, rows);
-    const int nb = (rows + 127) / 128;
+    const dim3 blk(lbmp::kAdjBX), grd((a.nx + lbmp::kAdjBX - 1) / lbmp::kAdjBX, rows);
     A.fin = (const float *)c->buf[cur];
     A.lam_in = lam1;
     A.lam_out = lam0;
-    lbmp::adjoint_seed_kernel<<<grd, blk, 0, s>>>(A);
+    lbmp::adjoint_step_kernel<true><<<grd, blk, 0, s>>>(A);
     ACK(cudaGetLastError());
     // backward, one segment at a time: recompute its levels from the
     // checkpoint, then run the reverse steps over them
     float *lam_next = lam0, *lam_prev = lam1;  // Lambda^{t+1}, Lambda^t
+    int64_t reversed = 0;  // the FP32 accumulators fold every kFold reverse steps
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
       const int64_t t0 = sg * every, n = std::min(every, nsteps - t0);
       ACK(cudaMemcpyAsync(segp, ckp + state * sg, state, cudaMemcpyDeviceToDevice, s));
@@ -539,24 +535,20 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
       for (int64_t t = n - 1; t >= 0; --t) {
         A.lam_in = lam_next;
         A.lam_out = lam_prev;
-        if (a.pressure) {  // the pressure columns of level t0 + t + 1
-          A.fin = (const float *)(segp + state * (t + 1));
-          lbmp::adjoint_neep_kernel<<<nb, 128, 0, s>>>(A);
-          ACK(cudaGetLastError());
-        }
         A.fin = (const float *)(segp + state * t);
-        lbmp::adjoint_step_kernel<<<grd, blk, 0, s>>>(A);
+        lbmp::adjoint_step_kernel<false><<<grd, blk, 0, s>>>(A);
         ACK(cudaGetLastError());
         std::swap(lam_next, lam_prev);
+        if (++reversed % lbmp::kFold == 0) {
+          lbmp::adjoint_fold_kernel<<<grd, blk, 0, s>>>(A);
+          ACK(cudaGetLastError());
+          c->launches++;
+        }
       }
-      c->launches += 2 * n + (a.pressure ? n : 0);
+      c->launches += 2 * n;
     }
-    if (a.pressure) {  // the pressure columns of level 0 (the rest state)
-      A.lam_in = lam_next;
-      A.fin = (const float *)segp;
-      lbmp::adjoint_neep_kernel<<<nb, 128, 0, s>>>(A);
-      ACK(cudaGetLastError());
-    }
+    lbmp::adjoint_fold_kernel<<<grd, blk, 0, s>>>(A);
+    ACK(cudaGetLastError());
     // d/d eps_z of G_eff through the mean porosity (pressure drive only)
     const double eps_term = (kp != 0.0) ? J * kp / (geff * c->eps_mean * nf) : 0.0;
     const size_t nn = (size_t)a.nx * a.ny;
@@ -566,10 +558,10 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
       ol = (double *)outs.p;
       oe = ol + nn;
     }
-    const dim3 g2((a.nx + 127) / 128, a.ny);
+    const dim3 g2((a.nx + lbmp::kAdjBX - 1) / lbmp::kAdjBX, a.ny);
     lbmp::adjoint_assemble_kernel<<<g2, blk, 0, s>>>(A, eps_term, ol, oe);
     ACK(cudaGetLastError());
-    c->launches += 3;
+    c->launches += 4;
     if (where == LBMP_HOST) {
       ACK(cudaMemcpyAsync(d_logk, ol, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
       ACK(cudaMemcpyAsync(d_eps, oe, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
