@@ -15,6 +15,9 @@ One JSON line on rank 0:
             lbmp_set_fields from host arrays + K steps + lbmp_permeability
   roofline  the fused step kernel against the measured HBM copy bandwidth
   cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample
+  adjoint   one gradient of k_g (lbmp_permeability_gradient) over 20000
+            steps of the 1024^2 two-component medium, with its backward
+            sweep against the HBM roofline
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
 With torchrun and N > 1 ranks every rank runs an independent replica (the
@@ -53,9 +56,15 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fp16-rounding", choices=["stochastic", "nearest"], default="stochastic")
-    ap.add_argument("--workload", choices=["shale", "batch"], default="shale",
+    ap.add_argument("--workload", choices=["shale", "batch", "adjoint"], default="shale",
                     help="shale: the 4096^2 fractured shale (default); batch: the batched sweep "
-                         "of two-component media of uneven sizes x Knudsen numbers")
+                         "of two-component media of uneven sizes x Knudsen numbers; adjoint: "
+                         "gradient of k_g on the 1024^2 two-component medium (a step is one "
+                         "gradient evaluation)")
+    ap.add_argument("--adjoint-steps", type=int, default=20000,
+                    help="time steps of the run the adjoint differentiates")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint object of the default line")
     ap.add_argument("--batch-media", type=int, default=256)
     ap.add_argument("--batch-kn", type=int, default=8)
     ap.add_argument("--kernel", choices=["auto", "staged", "direct"], default="auto",
@@ -328,6 +337,7 @@ def run_ours(args, ws, rank, local):
         res_other = time_storage(lbmp, torch, med, cfg, other, K, W, args.kernel,
                                  args.fp16_rounding)
     e2e = None if args.no_e2e else time_e2e(lbmp, torch, med, cfg, K)
+    adj = None if args.no_adjoint else adjoint_time(lbmp, torch, args.adjoint_steps)
 
     # slowest rank decides
     ms = reduce_max(res["ms"], "cuda")
@@ -341,7 +351,7 @@ def run_ours(args, ws, rank, local):
     nodes = res["nodes"]
     glups = whole_job_glups(ws, nodes, K, ms)
     peak, peak_kind = measured_peaks()
-    src = lbuild.source_hash()
+    src = lbuild.kernel_hash()
 
     def roofline(r, tag):
         per_launch_s = r["ms"] * 1e-3 / K          # one step kernel per time step
@@ -379,12 +389,131 @@ def run_ours(args, ws, rank, local):
                        "h2d_bytes_per_step": e2e["h2d"] / K, "d2h_bytes_per_step": e2e["d2h"] / K,
                        "what": "lbmp_set_fields from host float64 arrays + K steps + "
                                "lbmp_permeability to host, wall clock"}
+    if adj:
+        line["adjoint"] = adjoint_object(adj, peak, peak_kind)
     if not args.no_cpu and ws == 1:
         rate, steps, n, cores = oracle_rate(med, cfg, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "GLUPS", "cores": cores,
                                 "kind": "oracle",
                                 "sample": f"{n}x{n} crop of the workload, {steps} FP64 steps"}
     print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ adjoint
+ADJOINT_BYTES_PER_NODE = 36 + 36 + 8 + 16 + 36 + 48 / 32  # see adjoint_time()
+
+
+def adjoint_case(lbmp, n: int = 1024):
+    """The adjoint workload: two-component medium (correlation length 32,
+    matrix eps 0.2 / k_i 1e-5, inclusions eps 0.6 / k_i 1e-3, seed 2),
+    Kn = 0.1, pressure-driven in x, plates in y, Forchheimer on."""
+    from paper_1411_7051_gb300 import media
+    med = media.two_component(n, seed=2, kn=0.1)
+    cfg = lbmp.SimConfig(n, n, tau=0.8, bc_x=lbmp.BCX_PRESSURE, bc_y=lbmp.BCY_WALLS,
+                         rho_in=1.0005, rho_out=0.9995, forchheimer=1)
+    return med, cfg
+
+
+def adjoint_time(lbmp, torch, N: int, evals: int = 1, warm: int = 1, n: int = 1024):
+    """Times lbmp_permeability_gradient (N steps from rest) with CUDA events
+    on the library's stream, and the plain N-step run beside it.  The
+    backward sweep is the gradient time minus the forward and the recompute
+    passes (two timed forward runs).  Algorithmic bytes of one reverse step
+    per node: mu^{t+1} gathered 36, f^t pulled 36, medium 8, FP32
+    accumulators read + written 16, mu^t written 36, plus the FP64 fold
+    (8 + 32 + 8 bytes every 32 steps)."""
+    import math
+    med, cfg = adjoint_case(lbmp, n)
+    sim = lbmp.Sim(cfg)
+    sim.set_fields(med.eps, med.k_i, med.kn)
+    for _ in range(warm):
+        sim.permeability_gradient(min(N, 256))
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(sim.stream)
+    sim.set_fields(med.eps, med.k_i, med.kn)
+    sim.step(N)
+    e1.record(sim.stream)
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1)
+    l0 = sim.info().launches
+    t_grad = []
+    for _ in range(evals):
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record(sim.stream)
+        kg, gl, ge = sim.permeability_gradient(N)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        t_grad.append(e0.elapsed_time(e1))
+    launches = (sim.info().launches - l0) // evals
+    nodes = int(sim.info().fluid_nodes)
+    sim.close()
+    every = math.ceil(math.sqrt(N))
+    nseg = math.ceil(N / every)
+    state = 9 * 4 * (((n + 63) // 64) * 64) * n
+    tg = min(t_grad)
+    t_back = tg - 2.0 * t_fwd
+    return dict(ms_gradient=tg, ms_forward=t_fwd, ms_backward=t_back, nodes=nodes, N=N,
+                every=every, checkpoints=nseg, launches=int(launches), k_g=kg,
+                sum_abs_dlogk=float(gl.abs().sum()), sum_abs_deps=float(ge.abs().sum()),
+                device_bytes=(nseg + every + 3) * state + 24 * state // 36)
+
+
+def adjoint_object(r, peak, peak_kind):
+    from paper_1411_7051_gb300 import build as lbuild
+    back_s = r["ms_backward"] * 1e-3
+    achieved = ADJOINT_BYTES_PER_NODE * r["nodes"] * r["N"] / back_s / 1e9
+    tr = profiled_traffic("adjoint", lbuild.kernel_hash(lbuild.ADJOINT_KERNEL_FILES))
+    return {
+        "workload": "two-component 1024x1024 (corr. length 32, matrix eps 0.2 / k_i 1e-5, "
+                    "inclusions eps 0.6 / k_i 1e-3), Kn 0.1, pressure x, plates y, Forchheimer; "
+                    f"J = k_g after {r['N']} steps from rest; d/d ln k_i and d/d eps of every node",
+        "ms_per_gradient": r["ms_gradient"], "ms_forward_run": r["ms_forward"],
+        "ratio_to_forward_run": r["ms_gradient"] / r["ms_forward"],
+        "gradient_glups": r["nodes"] * r["N"] / (r["ms_gradient"] * 1e-3) / 1e9,
+        "checkpoint_every": r["every"], "checkpoints": r["checkpoints"],
+        "device_bytes": r["device_bytes"], "gpu_launches": r["launches"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                     "bytes_per_update": ADJOINT_BYTES_PER_NODE,
+                     "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                     "traffic_per_update": (tr["dram_bytes_per_launch"] / tr["nodes"] if tr else None),
+                     "kernel": "lbmp::adjoint_step_kernel<false> (+ fold)",
+                     "timing": "gradient minus forward and recompute passes, CUDA events"},
+        "k_g": r["k_g"],
+    }
+
+
+def run_adjoint(args, ws, rank, local):
+    """--workload adjoint: K gradient evaluations after W warm-up ones."""
+    import torch
+    from paper_1411_7051_gb300 import lbmp
+    torch.cuda.set_device(local)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl")
+    K, W = args.steps, max(3, args.warmup)
+    with ClockSampler(local) as clk:
+        r = adjoint_time(lbmp, torch, args.adjoint_steps, evals=K, warm=W)
+    ms = reduce_max(r["ms_gradient"], "cuda")
+    if rank == 0:
+        peak, kind = measured_peaks()
+        line = {
+            "metric": METRIC, "value": ws * r["nodes"] * r["N"] / (ms * 1e-3) / 1e9,
+            "unit": "GLUPS", "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "adjoint: gradient of k_g, one step = one gradient "
+                                   f"evaluation over {r['N']} time steps (forward, recompute, "
+                                   "reverse); value = time steps x nodes / gradient time",
+                       "nx": 1024, "ny": 1024, "l2": "working set > L2 per sweep, no flush"},
+            "adjoint": adjoint_object(r, peak, kind),
+            "gpu_launches": r["launches"] * K, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 
@@ -483,6 +612,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batch":
         run_batch(args, ws, rank, local)
+    elif args.workload == "adjoint":
+        run_adjoint(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -44,6 +44,21 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+STEP_KERNEL_FILES = ["kernels.cu", "kernels.h", "lattice.cuh", "staged.cuh"]
+ADJOINT_KERNEL_FILES = ["adjoint.cu", "kernels.h", "lattice.cuh"]
+
+
+def kernel_hash(files=STEP_KERNEL_FILES) -> str:
+    """Hash of the files that define a group of kernels (the time-step
+    kernels by default): the identity of the kernels whose DRAM traffic the
+    committed ncu summaries record."""
+    h = hashlib.sha256()
+    for name in files:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
 def _stamp() -> str:
     return os.path.join(OUT_DIR, "liblbmp.hash")
 
