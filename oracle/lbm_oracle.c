@@ -55,6 +55,9 @@ typedef struct orc_params {
   double rho0;   /* initial density */
   double rho_in, rho_out; /* densities imposed at x = 0 and x = nx-1 */
   int32_t forchheimer;    /* 1: keep the |u|u drag of Eq. 2; 0: Eq. 8 */
+  int32_t kn_model;       /* f_c: 0 Eq. 6-7 (second order), 1 Eq. 4-5 (first order) */
+  double kn_beta;         /* dynamic Kn: the pressure of a node is p0 (1 + kn_beta
+                             (rho - rho0)), its Kn = Kn(p0) p0 / p; 0: static Kn */
 } orc_params;
 
 typedef struct orc_sim {
@@ -62,7 +65,9 @@ typedef struct orc_sim {
   double *f;    /* post-stream populations at the current time level */
   double *fs;   /* post-collision scratch */
   double *eps;  /* porosity per node */
-  double *ka;   /* apparent permeability per node (may be +inf) */
+  double *ka;   /* apparent permeability per node at rho0 (may be +inf) */
+  double *ki;   /* intrinsic permeability per node (dynamic Kn) */
+  double *kn;   /* Knudsen number per node at rho0 (dynamic Kn) */
   int64_t steps;
 } orc_sim;
 
@@ -79,6 +84,39 @@ double orc_fc(double kn) {
 /* Eq. 3 with f_c of Eq. 6-7: k_a = k_i * f_c(Kn). */
 double orc_apparent_permeability(double k_i, double kn) {
   return k_i * orc_fc(kn);
+}
+
+/* Eq. 4-5: Klinkenberg's first-order factor f_c = 1 + b_k / p = 1 + 4 c Kn,
+ * with c = 1. */
+double orc_fc_first_order(double kn) { return 1.0 + 4.0 * kn; }
+
+/* f_c of the model selected in the parameters. */
+static double orc_fc_model(double kn, int32_t model) {
+  return model == 1 ? orc_fc_first_order(kn) : orc_fc(kn);
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 9-11: physical inputs of Kn (SI units in and out).               */
+/* ------------------------------------------------------------------ */
+/* Eq. 9: Kozeny-Carman intrinsic permeability [m^2] of packed spheres of
+ * diameter d [m]: k_d = C eps^3 / (1 - eps)^2 with C = d^2 / 180. */
+double orc_kozeny_carman(double eps, double d) {
+  const double C = d * d / 180.0;
+  return C * eps * eps * eps / ((1.0 - eps) * (1.0 - eps));
+}
+
+/* Eq. 10: mean free path [m] of a gas of viscosity mu [Pa s] at pressure p
+ * [Pa], temperature T [K], molar mass M [kg/mol]. */
+double orc_mean_free_path(double mu, double p, double T, double M) {
+  const double R = 8.314462618; /* J / (mol K) */
+  return mu / p * sqrt(3.14159265358979323846 * R * T / (2.0 * M));
+}
+
+/* Eq. 11 (Herd et al.): pore radius r [um] = 8.886e-2 sqrt(k [mD] / eps),
+ * here from k_d in m^2 to r in m (1 mD = 9.869e-16 m^2). */
+double orc_pore_radius(double k_d, double eps) {
+  const double k_mD = k_d / 9.869e-16;
+  return 8.886e-2 * sqrt(k_mD / eps) * 1e-6;
 }
 
 /* Lattice viscosities: nu_e = c_s^2 (tau - 1/2) with c_s^2 = 1/3 (dt = 1),
@@ -211,6 +249,18 @@ static int orc_is_wall_row(const orc_params *p, int y) {
   return p->bc_y == ORC_BC_WALLS && (y == 0 || y == p->ny - 1);
 }
 
+/* Apparent permeability of node j whose post-stream populations are f:
+ * the stored k_a, or with a dynamic Kn, k_i f_c(Kn(p0) p0 / p) with the
+ * node's pressure p / p0 = 1 + kn_beta (rho - rho0), rho = sum f (Eq. 16a). */
+static double orc_node_ka(const orc_sim *s, int64_t j, const double *f) {
+  const orc_params *p = &s->p;
+  if (p->kn_beta == 0.0) return s->ka[j];
+  double rho = 0.0;
+  for (int i = 0; i < 9; ++i) rho += f[i];
+  const double q = 1.0 + p->kn_beta * (rho - p->rho0);
+  return s->ki[j] * orc_fc_model(s->kn[j] / q, p->kn_model);
+}
+
 static void orc_apply_pressure(orc_sim *s) {
   const orc_params *p = &s->p;
   const int nx = p->nx, ny = p->ny;
@@ -219,10 +269,10 @@ static void orc_apply_pressure(orc_sim *s) {
     if (orc_is_wall_row(p, y)) continue;
     int64_t b0 = (int64_t)y * nx, n0 = b0 + 1;
     int64_t b1 = (int64_t)y * nx + nx - 1, n1 = b1 - 1;
-    orc_neep_node(s->f + n0 * 9, s->eps[n0], s->ka[n0], s->eps[b0], p->rho_in, p,
-                  s->f + b0 * 9);
-    orc_neep_node(s->f + n1 * 9, s->eps[n1], s->ka[n1], s->eps[b1], p->rho_out, p,
-                  s->f + b1 * 9);
+    orc_neep_node(s->f + n0 * 9, s->eps[n0], orc_node_ka(s, n0, s->f + n0 * 9), s->eps[b0],
+                  p->rho_in, p, s->f + b0 * 9);
+    orc_neep_node(s->f + n1 * 9, s->eps[n1], orc_node_ka(s, n1, s->f + n1 * 9), s->eps[b1],
+                  p->rho_out, p, s->f + b1 * 9);
   }
 }
 
@@ -241,8 +291,10 @@ orc_sim *orc_create(const orc_params *p) {
   s->fs = (double *)calloc(n * 9, sizeof(double));
   s->eps = (double *)calloc(n, sizeof(double));
   s->ka = (double *)calloc(n, sizeof(double));
-  if (!s->f || !s->fs || !s->eps || !s->ka) {
-    free(s->f); free(s->fs); free(s->eps); free(s->ka); free(s);
+  s->ki = (double *)calloc(n, sizeof(double));
+  s->kn = (double *)calloc(n, sizeof(double));
+  if (!s->f || !s->fs || !s->eps || !s->ka || !s->ki || !s->kn) {
+    free(s->f); free(s->fs); free(s->eps); free(s->ka); free(s->ki); free(s->kn); free(s);
     return NULL;
   }
   return s;
@@ -250,7 +302,7 @@ orc_sim *orc_create(const orc_params *p) {
 
 void orc_destroy(orc_sim *s) {
   if (!s) return;
-  free(s->f); free(s->fs); free(s->eps); free(s->ka); free(s);
+  free(s->f); free(s->fs); free(s->eps); free(s->ka); free(s->ki); free(s->kn); free(s);
 }
 
 void orc_set_threads(int n) {
@@ -278,7 +330,9 @@ void orc_set_fields(orc_sim *s, const double *eps, const double *k_i,
   int64_t n = (int64_t)p->nx * p->ny;
   for (int64_t j = 0; j < n; ++j) {
     s->eps[j] = eps[j];
-    s->ka[j] = orc_apparent_permeability(k_i[j], kn[j]);
+    s->ka[j] = k_i[j] * orc_fc_model(kn[j], p->kn_model); /* Eq. 3 */
+    s->ki[j] = k_i[j];
+    s->kn[j] = kn[j];
     for (int i = 0; i < 9; ++i) s->f[j * 9 + i] = ORC_W[i] * p->rho0;
   }
   s->steps = 0;
@@ -297,7 +351,8 @@ void orc_step(orc_sim *s, int64_t nsteps) {
       if (orc_is_wall_row(p, y)) continue;
       for (int x = 0; x < nx; ++x) {
         int64_t j = (int64_t)y * nx + x;
-        orc_collide_node(s->f + j * 9, s->eps[j], s->ka[j], p, s->fs + j * 9);
+        orc_collide_node(s->f + j * 9, s->eps[j], orc_node_ka(s, j, s->f + j * 9), p,
+                         s->fs + j * 9);
       }
     }
 #pragma omp parallel for schedule(static)
@@ -362,7 +417,7 @@ void orc_macroscopic(const orc_sim *s, double *rho, double *ux, double *uy) {
         continue;
       }
       double r, u[2];
-      orc_node_state(s->f + j * 9, s->eps[j], s->ka[j], p, &r, u, NULL);
+      orc_node_state(s->f + j * 9, s->eps[j], orc_node_ka(s, j, s->f + j * 9), p, &r, u, NULL);
       rho[j] = r;
       ux[j] = u[0];
       uy[j] = u[1];
@@ -406,7 +461,8 @@ double orc_permeability(const orc_sim *s, double *u_mean) {
     for (int x = 0; x < p->nx; ++x) {
       int64_t j = (int64_t)y * p->nx + x;
       double u[2];
-      orc_node_state(s->f + j * 9, s->eps[j], s->ka[j], p, NULL, u, NULL);
+      orc_node_state(s->f + j * 9, s->eps[j], orc_node_ka(s, j, s->f + j * 9), p, NULL, u,
+                     NULL);
       sum += u[0];
       count++;
     }
@@ -441,7 +497,8 @@ double orc_residual(const orc_sim *s, const double *ux_prev,
     for (int x = 0; x < p->nx; ++x) {
       int64_t j = (int64_t)y * p->nx + x;
       double u[2];
-      orc_node_state(s->f + j * 9, s->eps[j], s->ka[j], p, NULL, u, NULL);
+      orc_node_state(s->f + j * 9, s->eps[j], orc_node_ka(s, j, s->f + j * 9), p, NULL, u,
+                     NULL);
       double dx = u[0] - ux_prev[j], dy = u[1] - uy_prev[j];
       num += dx * dx + dy * dy;
       den += u[0] * u[0] + u[1] * u[1];

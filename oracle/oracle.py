@@ -50,6 +50,7 @@ class Params(ctypes.Structure):
         ("rho0", ctypes.c_double),
         ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
         ("forchheimer", ctypes.c_int32),
+        ("kn_model", ctypes.c_int32), ("kn_beta", ctypes.c_double),
     ]
 
 
@@ -63,6 +64,11 @@ def _load(path: str):
     P = ctypes.POINTER(Params)
     L.orc_fc.restype = ctypes.c_double
     L.orc_fc.argtypes = [ctypes.c_double]
+    for name, nargs in (("orc_fc_first_order", 1), ("orc_kozeny_carman", 2),
+                        ("orc_mean_free_path", 4), ("orc_pore_radius", 2)):
+        fn = getattr(L, name)
+        fn.restype = ctypes.c_double
+        fn.argtypes = [ctypes.c_double] * nargs
     L.orc_apparent_permeability.restype = ctypes.c_double
     L.orc_apparent_permeability.argtypes = [ctypes.c_double, ctypes.c_double]
     L.orc_node_state.argtypes = [_D, ctypes.c_double, ctypes.c_double, P, _D, _D, _D]
@@ -129,18 +135,41 @@ def _vec(x) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
 
 
+KN_BKC, KN_FIRST_ORDER = 0, 1
+
+
 def make_params(nx, ny, tau=0.8, J=1.0, G=(0.0, 0.0), bc_x=BC_PERIODIC,
                 bc_y=BC_PERIODIC, rho0=1.0, rho_in=1.0, rho_out=1.0,
-                forchheimer=0) -> Params:
+                forchheimer=0, kn_model=KN_BKC, kn_beta=0.0) -> Params:
     return Params(int(nx), int(ny), float(tau), float(J), float(G[0]), float(G[1]),
                   int(bc_x), int(bc_y), float(rho0), float(rho_in), float(rho_out),
-                  int(forchheimer))
+                  int(forchheimer), int(kn_model), float(kn_beta))
 
 
 # ---- closed forms -------------------------------------------------------
 def fc(kn: float) -> float:
     """Eq. 6-7 correction factor f_c(Kn), b = -1."""
     return lib().orc_fc(float(kn))
+
+
+def fc_first_order(kn: float) -> float:
+    """Eq. 4-5: f_c = 1 + 4 Kn."""
+    return float(lib().orc_fc_first_order(float(kn)))
+
+
+def kozeny_carman(eps: float, d: float) -> float:
+    """Eq. 9: k_d [m^2] of packed spheres of diameter d [m]."""
+    return float(lib().orc_kozeny_carman(float(eps), float(d)))
+
+
+def mean_free_path(mu: float, p: float, T: float, M: float) -> float:
+    """Eq. 10: lambda [m] (mu Pa s, p Pa, T K, M kg/mol)."""
+    return float(lib().orc_mean_free_path(float(mu), float(p), float(T), float(M)))
+
+
+def pore_radius(k_d: float, eps: float) -> float:
+    """Eq. 11: r [m] from k_d [m^2] (Herd et al.)."""
+    return float(lib().orc_pore_radius(float(k_d), float(eps)))
 
 
 def apparent_permeability(k_i: float, kn: float) -> float:
