@@ -65,6 +65,8 @@ def parse():
                     help="time steps of the run the adjoint differentiates")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint object of the default line")
+    ap.add_argument("--no-dynamic", action="store_true",
+                    help="skip the dynamic-Kn object of the default line")
     ap.add_argument("--batch-media", type=int, default=256)
     ap.add_argument("--batch-kn", type=int, default=8)
     ap.add_argument("--kernel", choices=["auto", "staged", "direct"], default="auto",
@@ -236,7 +238,15 @@ def config_dict(args, cfg, storage):
 
 
 # ------------------------------------------------------------- GPU (ours)
-def time_storage(lbmp, torch, med, cfg, storage, K, W, kernel, rounding="stochastic"):
+def kn_beta_for(cfg, p_ratio: float = 2.0) -> float:
+    """beta of the dynamic Kn that makes the inlet pressure p_ratio times
+    the outlet one (p / p0 = 1 + beta (rho - rho0), rho0 = 1)."""
+    a, b = cfg["rho_in"] - 1.0, cfg["rho_out"] - 1.0
+    return (p_ratio - 1.0) / (a - p_ratio * b)
+
+
+def time_storage(lbmp, torch, med, cfg, storage, K, W, kernel, rounding="stochastic",
+                 kn_beta=0.0):
     st = lbmp.STORE_FP32 if storage == "fp32" else lbmp.STORE_FP16
     sc = lbmp.SimConfig(cfg["nx"], cfg["ny"], tau=cfg["tau"], bc_x=cfg["bc_x"],
                         bc_y=cfg["bc_y"], rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
@@ -244,7 +254,7 @@ def time_storage(lbmp, torch, med, cfg, storage, K, W, kernel, rounding="stochas
                         kernel={"auto": lbmp.KERNEL_AUTO, "staged": lbmp.KERNEL_STAGED,
                                 "direct": lbmp.KERNEL_DIRECT}[kernel],
                         fp16_rounding=(lbmp.ROUND_STOCHASTIC if rounding == "stochastic"
-                                       else lbmp.ROUND_NEAREST))
+                                       else lbmp.ROUND_NEAREST), kn_beta=kn_beta)
     sim = lbmp.Sim(sc)
     sim.set_fields(med.eps, med.k_i, med.kn)
     sim.step(W)
@@ -337,6 +347,10 @@ def run_ours(args, ws, rank, local):
         res_other = time_storage(lbmp, torch, med, cfg, other, K, W, args.kernel,
                                  args.fp16_rounding)
     e2e = None if args.no_e2e else time_e2e(lbmp, torch, med, cfg, K)
+    dyn = None
+    if not args.no_dynamic:
+        dyn = time_storage(lbmp, torch, med, cfg, "fp32", K, W, "auto",
+                           kn_beta=kn_beta_for(cfg))
     adj = None if args.no_adjoint else adjoint_time(lbmp, torch, args.adjoint_steps)
 
     # slowest rank decides
@@ -389,6 +403,18 @@ def run_ours(args, ws, rank, local):
                        "h2d_bytes_per_step": e2e["h2d"] / K, "d2h_bytes_per_step": e2e["d2h"] / K,
                        "what": "lbmp_set_fields from host float64 arrays + K steps + "
                                "lbmp_permeability to host, wall clock"}
+    if dyn:
+        g3 = ws * dyn["nodes"] * K / (dyn["ms"] * 1e-3) / 1e9
+        r = roofline(dyn, "StoreF32")
+        r["traffic"] = r["traffic_per_update"] = None   # recorded for the static kernel only
+        r["kernel"] = "lbmp::step_kernel<StoreF32, false, true> (dynamic Kn)"
+        line["fp32_dynamic_kn"] = {
+            "value": g3, "unit": "GLUPS", "ms_per_step": dyn["ms"] / K,
+            "what": "same workload with Kn per node and step from the local pressure "
+                    f"(p/p0 = 1 + beta (rho - rho0), beta {kn_beta_for(cfg):.1f}: inlet "
+                    "pressure twice the outlet one; the medium's Kn taken at p0), f_c of "
+                    "Eq. 6-7 in FP32 at every step",
+            "ratio_to_static": g3 / glups, "roofline": r, "k_g": dyn["k_g"]}
     if adj:
         line["adjoint"] = adjoint_object(adj, peak, peak_kind)
     if not args.no_cpu and ws == 1:

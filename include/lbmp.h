@@ -71,6 +71,10 @@ typedef int32_t lbmp_status;
 #define LBMP_HOST 0
 #define LBMP_DEVICE 1
 
+/* correction factor f_c of Eq. 3 */
+#define LBMP_KN_BKC 0         /* Beskok-Karniadakis-Civan, Eq. 6-7 (b = -1): the paper's */
+#define LBMP_KN_FIRST_ORDER 1 /* Klinkenberg's first-order Eq. 4-5: f_c = 1 + 4 Kn (c = 1) */
+
 typedef struct lbmp_params {
   int32_t nx, ny;       /* lattice size; nx, ny >= 1 */
   double tau;           /* relaxation time of Eq. 12, > 0.5 */
@@ -86,9 +90,21 @@ typedef struct lbmp_params {
   int32_t fp16_log2_scale; /* s of S = 2^s for FP16 storage; 0 = automatic */
   int32_t fp16_rounding;   /* LBMP_ROUND_*: how FP16 stores round */
   int32_t kernel;          /* LBMP_KERNEL_*: implementation of the step */
-  int32_t reserved;        /* must be 0 */
+  int32_t kn_model;        /* LBMP_KN_*: the correlation f_c(Kn) */
   uint64_t seed;           /* stream of the stochastic rounding (any value) */
   void *stream;         /* cudaStream_t for all work; NULL = a private stream */
+  double kn_beta;       /* dynamic Knudsen number ("dynamic apparent permeability",
+                           Section IV.B and V): 0 keeps the Kn given to
+                           lbmp_set_fields.  Otherwise that Kn belongs to the
+                           pressure p0 of density rho0, a node's pressure is
+                           p = p0 (1 + kn_beta (rho - rho0)) with rho its density
+                           at the time level, its Kn = Kn(p0) p0 / p (the mean
+                           free path of Eq. 10 is inversely proportional to p)
+                           and k_a = k_i f_c(Kn) is formed at every step.  Needs
+                           the direct kernel (AUTO picks it); 1 + kn_beta
+                           (rho - rho0) must stay > 0 (checked for rho_in and
+                           rho_out), else velocities turn non-finite (ENAN).
+                           Not available to lbmp_batch_* and the adjoint. */
 } lbmp_params;
 
 typedef struct lbmp_info {
@@ -171,6 +187,35 @@ lbmp_status lbmp_mass(lbmp_ctx *ctx, double *m);
 /* Eq. 6-7 correction factor f_c(Kn), b = -1, f_c(0) = 1.  Host function;
  * returns NaN for Kn < 0 or NaN. */
 double lbmp_fc(double kn);
+/* f_c(Kn) of the correlation kn_model (LBMP_KN_*).  Host; NaN for Kn < 0,
+ * NaN, or an unknown model. */
+double lbmp_fc_model(int32_t kn_model, double kn);
+
+/* ---------------------------------------------------------------------
+ * Physical inputs of the Knudsen number (Section II, Eq. 9-11).  Host
+ * functions, SI units.
+ * --------------------------------------------------------------------- */
+/* Eq. 9, Kozeny-Carman: intrinsic permeability [m^2] of packed spheres of
+ * diameter d [m], k_d = (d^2 / 180) eps^3 / (1 - eps)^2.  NaN outside
+ * 0 <= eps < 1 or for d < 0. */
+double lbmp_kozeny_carman(double eps, double d);
+/* Eq. 10: mean free path [m] of a gas of viscosity mu [Pa s] at pressure
+ * p [Pa], temperature T [K] and molar mass M [kg/mol],
+ * lambda = (mu / p) sqrt(pi R T / (2 M)).  NaN for non-positive inputs. */
+double lbmp_mean_free_path(double mu, double p, double T, double M);
+/* Eq. 11 (Herd et al.): characteristic pore radius [m] from k_d [m^2],
+ * r [um] = 8.886e-2 sqrt(k_d [mD] / eps), 1 mD = 9.869e-16 m^2.  NaN for
+ * k_d < 0 or eps <= 0. */
+double lbmp_pore_radius(double k_d, double eps);
+/* Lattice medium from physical data, for lbmp_set_fields: per node i of n,
+ * k_d = Eq. 9 (eps[i], d[i]), k_i[i] = k_d / dx^2 (lattice units, dx [m]
+ * the node spacing) and kn[i] = lambda / r with r = Eq. 11 (k_d, eps[i]) and
+ * lambda [m] the mean free path (Eq. 10).  Impermeable nodes (eps = 0) get
+ * k_i = 1, kn = 0 (unused); open pores (eps = 1) k_i = +inf, kn = 0.  Host
+ * arrays.  Errors: EINVAL (NULL pointer, eps outside [0, 1], d <= 0 at a
+ * porous node, lambda < 0, dx <= 0). */
+lbmp_status lbmp_physical_medium(int64_t n, const double *eps, const double *d, double lambda,
+                                 double dx, double *k_i, double *kn);
 
 /* Checkpoint: bytes of a state blob (header + raw population buffer). */
 lbmp_status lbmp_state_size(lbmp_ctx *ctx, size_t *bytes);
@@ -207,8 +252,8 @@ lbmp_status lbmp_get_info(lbmp_ctx *ctx, lbmp_info *out);
  * parameter derivatives are summed in FP32 over at most 32 steps, then in
  * FP64.  The context is left at time level nsteps of a run from rest (its
  * previous state is replaced).  Needs FP32 storage.  Synchronous.
- * Errors: EINVAL (NULL pointer, nsteps < 1, every < 0, FP16 storage),
- * ESTATE (no fields set), ENOMEM, ENAN, ETIMEOUT, ECUDA. */
+ * Errors: EINVAL (NULL pointer, nsteps < 1, every < 0, FP16 storage, a
+ * dynamic Kn), ESTATE (no fields set), ENOMEM, ENAN, ETIMEOUT, ECUDA. */
 lbmp_status lbmp_permeability_gradient(lbmp_ctx *ctx, int64_t nsteps, int64_t every,
                                        double *k_g, double *d_logk, double *d_eps,
                                        int32_t where);
@@ -270,7 +315,8 @@ lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out);
  * law over the whole domain with eps p = c_s^2 rho for the pressure drop),
  * in FP64, from:
  *   p            lattice size, tau, J, G, boundary kinds, rho0, rho_in,
- *                rho_out, forchheimer (other fields ignored);
+ *                rho_out, forchheimer, kn_model, kn_beta (other fields
+ *                ignored; a dynamic Kn takes each node's density from f);
  *   f            device, [9][ny][nx] float64 post-stream populations, as
  *                lbmp_populations(..., LBMP_DEVICE) returns them;
  *   eps,k_i,kn   device, [ny][nx] float64 medium as for lbmp_set_fields;

@@ -456,6 +456,8 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
     if (!c->fields_set) return afail(LBMP_ESTATE, "lbmp_permeability_gradient: no fields set");
     if (c->p.storage != LBMP_STORE_FP32)
       return afail(LBMP_EINVAL, "lbmp_permeability_gradient needs FP32 storage");
+    if (c->p.kn_beta != 0.0)
+      return afail(LBMP_EINVAL, "lbmp_permeability_gradient: a dynamic Kn is not available");
     ACK(cudaSetDevice(c->device));
     if (every == 0) every = (int64_t)std::ceil(std::sqrt((double)nsteps));
     every = std::min(every, nsteps);

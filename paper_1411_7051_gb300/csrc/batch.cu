@@ -442,6 +442,8 @@ lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32
     *out = nullptr;
     if (count < 1) return bfail(LBMP_EINVAL, "count must be >= 1");
     lbmp_params p = *pin;
+    if (p.kn_beta != 0.0)
+      return bfail(LBMP_EINVAL, "lbmp_batch_*: a dynamic Kn (kn_beta != 0) is not available");
     if (p.J == 0.0) p.J = 1.0;
     if (p.rho0 == 0.0) p.rho0 = 1.0;
     // validate the shared parameters through the single-lattice rules
@@ -516,6 +518,9 @@ lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32
       a.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
       a.seed_hi = (uint32_t)(p.seed >> 32);
       a.test_drop_tile = -1;
+      a.kn_model = p.kn_model;
+      a.kn_beta = 0.0f;
+      a.kn0 = nullptr;
       I.rows = walls ? ny[i] - 2 : ny[i];
       I.index = i;
       b->fluid_nodes[i] = (long long)nx[i] * I.rows;
@@ -593,8 +598,9 @@ lbmp_status lbmp_batch_set_fields(lbmp_batch *b, int32_t i, const double *eps, c
     if (e == cudaSuccess)
       e = cudaMemsetAsync((void *)I.med, 0, (size_t)a.plane * sizeof(float2), b->stream);
     if (e == cudaSuccess)
-      e = lbmp::launch_medium(de, dk, dn, a.nx, a.ny, a.pitch, a.y0, y_hi, (float2 *)I.med,
-                              b->d_flag, b->d_med_partials, b->stream);
+      e = lbmp::launch_medium(de, dk, dn, a.nx, a.ny, a.pitch, a.y0, y_hi, b->p.kn_model,
+                              nullptr, 1.0, (float2 *)I.med, b->d_flag, b->d_med_partials,
+                              b->stream);
     if (e == cudaSuccess)
       e = lbmp::launch_finalize(b->d_med_partials, lbmp::medium_blocks(a.nx, a.ny), lbmp::kNQ,
                                 b->d_med_results, b->stream, lbmp::kMediumMaxMask);

@@ -24,6 +24,7 @@ struct lbmp_ctx {
   void *buf[2] = {nullptr, nullptr};
   int cur = 0;
   float2 *med = nullptr;
+  float *kn0 = nullptr;         // dynamic Kn only: Kn at p0 per node
   float2 *uprev = nullptr;
   double *partials = nullptr;
   int partials_blocks = 0;
@@ -72,6 +73,9 @@ struct lbmp_ctx {
     a.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p.seed >> 32);
     a.test_drop_tile = drop_tile;
+    a.kn_model = p.kn_model;
+    a.kn_beta = (float)p.kn_beta;
+    a.kn0 = kn0;
     return a;
   }
   int rows() const { return y_hi - y_lo; }

@@ -29,7 +29,9 @@ constexpr int kMediumBX = 256;
 // are block-uniform branches inside pull_node.  The stochastic-rounding
 // bits of time level t come from *tctr + k (the counter is advanced by
 // bump_kernel after a group of launches).
-template <class S, bool SR>
+// DYN: Knudsen number per node and step from the local pressure (the
+// medium holds 1/k_i, a.kn0 the Kn at p0).
+template <class S, bool SR, bool DYN>
 __global__ void __launch_bounds__(kStepBX)
     step_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
                 typename S::T *__restrict__ fout, const float2 *__restrict__ med,
@@ -39,12 +41,15 @@ __global__ void __launch_bounds__(kStepBX)
   const long long row = (long long)y * a.pitch;
   float d[kStepNPT][9];
   float2 m[kStepNPT];
+  float k0[kStepNPT];
 #pragma unroll
   for (int j = 0; j < kStepNPT; ++j) {
     const int x = xb + j * kStepBX;
+    k0[j] = 0.0f;
     if (x < a.nx) {
       pull_node<S>(fin, a, x, y, d[j]);
       m[j] = med[row + x];
+      if (DYN) k0[j] = a.kn0[row + x];
     }
   }
   uint32_t ts = 0;
@@ -56,8 +61,9 @@ __global__ void __launch_bounds__(kStepBX)
   for (int j = 0; j < kStepNPT; ++j) {
     const int x = xb + j * kStepBX;
     if (x >= a.nx) continue;
-    if (a.pressure && (x == 0 || x == a.nx - 1)) pressure_node<S>(fin, med, a, x, y, m[j].x, d[j]);
-    const NodeState s = node_state(d[j], m[j].x, m[j].y, a);
+    if (a.pressure && (x == 0 || x == a.nx - 1))
+      pressure_node<S, DYN>(fin, med, a, x, y, m[j].x, d[j]);
+    const NodeState s = node_state<DYN>(d[j], m[j].x, m[j].y, a, k0[j]);
     collide<S::kHiLo>(d[j], s, a);
     typename S::T *o = fout + row + x;
     const uint32_t h = SR ? mix32((uint32_t)(row + x) ^ ts) : 0u;
@@ -75,15 +81,27 @@ cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const
   if (rows <= 0 || a.nx <= 0) return cudaSuccess;
   dim3 block(kStepBX);
   dim3 grid((a.nx + kStepBX * kStepNPT - 1) / (kStepBX * kStepNPT), rows);
-  if (storage == 0)
-    step_kernel<StoreF32, false><<<grid, block, 0, s>>>(a, (const float *)fin, (float *)fout,
-                                                        med, tctr, k);
-  else if (sr)
-    step_kernel<StoreF16, true><<<grid, block, 0, s>>>(a, (const __half *)fin, (__half *)fout,
-                                                       med, tctr, k);
-  else
-    step_kernel<StoreF16, false><<<grid, block, 0, s>>>(a, (const __half *)fin,
-                                                        (__half *)fout, med, tctr, k);
+  const bool dyn = a.kn0 != nullptr;
+  const float *f32i = (const float *)fin;
+  float *f32o = (float *)fout;
+  const __half *f16i = (const __half *)fin;
+  __half *f16o = (__half *)fout;
+  if (storage == 0) {
+    if (dyn)
+      step_kernel<StoreF32, false, true><<<grid, block, 0, s>>>(a, f32i, f32o, med, tctr, k);
+    else
+      step_kernel<StoreF32, false, false><<<grid, block, 0, s>>>(a, f32i, f32o, med, tctr, k);
+  } else if (sr) {
+    if (dyn)
+      step_kernel<StoreF16, true, true><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k);
+    else
+      step_kernel<StoreF16, true, false><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k);
+  } else {
+    if (dyn)
+      step_kernel<StoreF16, false, true><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k);
+    else
+      step_kernel<StoreF16, false, false><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k);
+  }
   return cudaGetLastError();
 }
 
@@ -181,10 +199,18 @@ __global__ void __launch_bounds__(kMacroBX)
         for (int i = 0; i < 9; ++i) o.pops[i * n + j] = 0.0;
     } else {
       float d[9];
-      const float2 m = med[(long long)y * a.pitch + x];
+      const long long jp = (long long)y * a.pitch + x;
+      const float2 m = med[jp];
       pull_node<S>(fin, a, x, y, d);
-      if (a.pressure && (x == 0 || x == a.nx - 1)) pressure_node<S>(fin, med, a, x, y, m.x, d);
-      const NodeState s = node_state(d, m.x, m.y, a);
+      const bool col = a.pressure && (x == 0 || x == a.nx - 1);
+      NodeState s;
+      if (a.kn0) {  // dynamic Kn
+        if (col) pressure_node<S, true>(fin, med, a, x, y, m.x, d);
+        s = node_state<true>(d, m.x, m.y, a, a.kn0[jp]);
+      } else {
+        if (col) pressure_node<S, false>(fin, med, a, x, y, m.x, d);
+        s = node_state<false>(d, m.x, m.y, a);
+      }
       const float drho = s.drho_s * a.inv_scale;
       (void)drho;
       if (o.rho) o.rho[j] = (double)s.rho;
@@ -270,36 +296,46 @@ cudaError_t launch_finalize(const double *partials, int nblocks, int nq, double 
 __global__ void __launch_bounds__(kMediumBX)
     medium_kernel(const double *__restrict__ eps, const double *__restrict__ k_i,
                   const double *__restrict__ kn, int nx, int ny, int pitch, int y_lo,
-                  int y_hi, float2 *__restrict__ med, unsigned *bad,
-                  double *__restrict__ partials) {
+                  int y_hi, int kn_model, float *__restrict__ kn0, double kn_scale_max,
+                  float2 *__restrict__ med, unsigned *bad, double *__restrict__ partials) {
   const int y = blockIdx.y;
   const int x = blockIdx.x * kMediumBX + threadIdx.x;
   double v[kNQ] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (x < nx) {
     const long long j = (long long)y * nx + x;
     float2 out = make_float2(0.0f, 0.0f);
+    float kn_out = 0.0f;
     if (y >= y_lo && y < y_hi) {
       const double e = eps[j], k = k_i[j], K = kn[j];
       unsigned flags = 0;
       if (!(e >= 0.0 && e <= 1.0)) flags |= 1u;               // also NaN
       if (!(k > 0.0)) flags |= 2u;                             // NaN, <= 0
       if (!(K >= 0.0 && isfinite(K))) flags |= 4u;
-      double inv_k = 0.0;
+      double inv_k = 0.0, ka_max = 0.0;
       if (!flags) {
-        const double ka = k * fc_bkc(K);                       // Eq. 3, 6-7
-        if (!(ka >= 1e-15)) flags |= 8u;                       // 1/k_a must fit FP32 math
-        inv_k = isinf(ka) ? 0.0 : 1.0 / ka;
+        if (kn0) {  // dynamic Kn: 1/k_i stored, k_a formed at every step
+          if (!(k >= 1e-15)) flags |= 8u;
+          inv_k = isinf(k) ? 0.0 : 1.0 / k;
+          ka_max = k * fc_model(K * kn_scale_max, kn_model);  // at the lowest imposed pressure
+          kn_out = (float)K;
+        } else {
+          const double ka = k * fc_model(K, kn_model);         // Eq. 3 with Eq. 6-7 or 4-5
+          if (!(ka >= 1e-15)) flags |= 8u;                     // 1/k_a must fit FP32 math
+          inv_k = isinf(ka) ? 0.0 : 1.0 / ka;
+          ka_max = ka;
+        }
       }
       if (flags) atomicOr(bad, flags);
       out = make_float2((float)e, (float)inv_k);
       v[0] = e;
       v[1] = 1.0;
       if (!flags && e > 0.0) {
-        if (inv_k > 0.0) v[2] = 1.0 / inv_k;  // largest finite k_a (max-reduced)
-        else v[3] = 1.0;                     // open pores (k_a = inf)
+        if (inv_k > 0.0) v[2] = ka_max;  // largest finite k_a (max-reduced)
+        else v[3] = 1.0;                 // open pores (k_a = inf)
       }
     }
     med[(long long)y * pitch + x] = out;
+    if (kn0) kn0[(long long)y * pitch + x] = kn_out;
   }
   block_reduce_store<kMediumBX>(v, partials, kMediumMaxMask);
 }
@@ -307,12 +343,13 @@ __global__ void __launch_bounds__(kMediumBX)
 int medium_blocks(int nx, int ny) { return ((nx + kMediumBX - 1) / kMediumBX) * ny; }
 
 cudaError_t launch_medium(const double *eps, const double *k_i, const double *kn,
-                          int nx, int ny, int pitch, int y_lo, int y_hi, float2 *med,
-                          unsigned *bad, double *partials, cudaStream_t s) {
+                          int nx, int ny, int pitch, int y_lo, int y_hi, int kn_model,
+                          float *kn0, double kn_scale_max, float2 *med, unsigned *bad,
+                          double *partials, cudaStream_t s) {
   dim3 block(kMediumBX);
   dim3 grid((nx + kMediumBX - 1) / kMediumBX, ny);
-  medium_kernel<<<grid, block, 0, s>>>(eps, k_i, kn, nx, ny, pitch, y_lo, y_hi, med, bad,
-                                       partials);
+  medium_kernel<<<grid, block, 0, s>>>(eps, k_i, kn, nx, ny, pitch, y_lo, y_hi, kn_model, kn0,
+                                       kn_scale_max, med, bad, partials);
   return cudaGetLastError();
 }
 

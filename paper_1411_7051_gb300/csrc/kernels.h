@@ -31,6 +31,12 @@ __host__ __device__ inline double fc_bkc(double kn) {
   return (1.0 + alpha * kn) * (1.0 + 4.0 * kn / (1.0 - slip_b * kn));
 }
 
+// f_c of the selected correlation: 0 Eq. 6-7, 1 Klinkenberg's first-order
+// Eq. 4-5 (f_c = 1 + 4 c Kn, c = 1).
+__host__ __device__ inline double fc_model(double kn, int model) {
+  return model == 1 ? 1.0 + 4.0 * kn : fc_bkc(kn);
+}
+
 // One time step over rows [a.y0, a.y0 + rows).  sr: FP16 stochastic
 // rounding with the bits of time level *tctr + k.
 cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
@@ -64,14 +70,17 @@ cudaError_t launch_macro(int storage, const StepArgs &a, const void *fin,
 cudaError_t launch_finalize(const double *partials, int nblocks, int nq, double *out,
                             cudaStream_t s, unsigned max_mask = 0u);
 
-// Medium precompute: (eps, k_i, Kn) -> float2 (eps, 1/k_a); flags invalid
-// values in *bad; FP64 block partials over rows [y_lo, y_hi): sum eps, fluid
-// nodes, max finite k_a (max-reduced, kMediumMaxMask), open-pore count.
+// Medium precompute: (eps, k_i, Kn) -> float2 (eps, 1/k_a) with f_c of
+// kn_model; with kn0 != NULL (dynamic Kn) float2 (eps, 1/k_i) and kn0 = Kn.
+// Flags invalid values in *bad; FP64 block partials over rows [y_lo, y_hi):
+// sum eps, fluid nodes, max finite k_a (max-reduced, kMediumMaxMask; with a
+// dynamic Kn at Kn * kn_scale_max), open-pore count.
 constexpr unsigned kMediumMaxMask = 1u << 2;
 int medium_blocks(int nx, int ny);
 cudaError_t launch_medium(const double *eps, const double *k_i, const double *kn,
-                          int nx, int ny, int pitch, int y_lo, int y_hi, float2 *med,
-                          unsigned *bad, double *partials, cudaStream_t s);
+                          int nx, int ny, int pitch, int y_lo, int y_hi, int kn_model,
+                          float *kn0, double kn_scale_max, float2 *med, unsigned *bad,
+                          double *partials, cudaStream_t s);
 
 // Inverse of the pull: write a post-collision buffer whose pull gives the
 // post-stream populations f ([9][ny][nx] float64).

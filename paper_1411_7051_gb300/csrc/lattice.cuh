@@ -46,6 +46,10 @@ struct StepArgs {
   uint32_t seed_lo, seed_hi;  // stochastic rounding stream
   int test_drop_tile;   // staged kernel: tile whose copies are withheld (-1: none);
                         // exercises the bounded waits in tests
+  int kn_model;         // f_c: 0 Eq. 6-7 (second order), 1 Eq. 4-5 (first order)
+  float kn_beta;        // dynamic Kn: p / p0 = 1 + kn_beta (rho - rho0)
+  const float *kn0;     // dynamic Kn: [ny][pitch] Kn at p0 (medium then holds 1/k_i);
+                        // NULL for a static Kn (medium holds 1/k_a)
 };
 
 // ------------------------------------------------ hardware approximations
@@ -72,6 +76,16 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   h *= 0xc2b2ae35u;
   h ^= h >> 16;
   return h;
+}
+
+// f_c of Eq. 6-7 (b = -1; model 0) or of Eq. 4-5 (model 1) in FP32, for the
+// Knudsen number of a node at its current pressure (dynamic Kn).  At Kn = 0
+// the power Kn^-0.4348 is +inf, alpha 0 and f_c exactly 1.
+__device__ __forceinline__ float fc_f32(float kn, int model) {
+  if (model == 1) return fmaf(4.0f, kn, 1.0f);
+  const float t = exp2f(-0.4348f * log2f(kn));
+  const float alpha = 1.358f / fmaf(0.170f, t, 1.0f);
+  return fmaf(alpha, kn, 1.0f) * (1.0f + 4.0f * kn / (1.0f + kn));
 }
 
 // ----------------------------------------------------------------- storage
@@ -180,8 +194,12 @@ struct NodeState {
 // Eq. 16a, Eq. 16b solved for u (Eq. 17, or u = v / (c0 + sqrt(c0^2 +
 // c1|v|)) with the Forchheimer term), and F of Eq. 2.  eps = 0 is an
 // impermeable node: u = 0 and F = -2 m / rho (Eq. 16b with u = 0).
+// DYN: inv_k is 1/k_i and kn0 the node's Kn at p0; its apparent
+// permeability k_a = k_i f_c(kn0 p0 / p) (Eq. 3) follows the pressure
+// p / p0 = 1 + kn_beta (rho - rho0) of the node.
+template <bool DYN = false>
 __device__ __forceinline__ NodeState node_state(const float d[9], float eps, float inv_k,
-                                                const StepArgs &a) {
+                                                const StepArgs &a, float kn0 = 0.0f) {
   NodeState s;
   s.drho_s = ((d[0] + (d[1] + d[3])) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
   // sum_i w_i e_i = 0, so the momentum of the deviations is the momentum.
@@ -192,6 +210,10 @@ __device__ __forceinline__ NodeState node_state(const float d[9], float eps, flo
   s.rho = fmaf(s.drho_s, a.inv_scale, a.rho0);
   const float c = a.inv_scale * rcp_approx(s.rho);  // 1 / (S rho)
   if (eps > 0.0f) {
+    if (DYN) {
+      const float q = fmaf(a.kn_beta, s.drho_s * a.inv_scale, 1.0f);
+      inv_k = inv_k / fc_f32(kn0 / q, a.kn_model);
+    }
     s.ieps = rcp_approx(eps);
     const float eGx = eps * a.Gx, eGy = eps * a.Gy;
     const float vx = fmaf(0.5f, eGx, mx * c);
@@ -306,15 +328,16 @@ __device__ __forceinline__ void equilibrium_dev(float drho, float rho, float ux,
 // Pressure column (non-equilibrium extrapolation, Guo, Zheng & Shi 2002),
 // stored units: d_b = d_n + S (deq(rho_b, u_n; eps_b) - deq(rho_n, u_n;
 // eps_n)), n the adjacent interior node and rho_b the imposed density.
-template <class S>
+template <class S, bool DYN = false>
 __device__ __forceinline__ void pressure_node(const typename S::T *__restrict__ fin,
                                            const float2 *__restrict__ med, const StepArgs &a,
                                            int xb, int y, float eps_b, float d[9]) {
   const int xn = (xb == 0) ? 1 : a.nx - 2;
-  const float2 mn = med[(long long)y * a.pitch + xn];
+  const long long jn = (long long)y * a.pitch + xn;
+  const float2 mn = med[jn];
   float dn[9];
   pull_node<S>(fin, a, xn, y, dn);
-  const NodeState sn = node_state(dn, mn.x, mn.y, a);
+  const NodeState sn = node_state<DYN>(dn, mn.x, mn.y, a, DYN ? a.kn0[jn] : 0.0f);
   const float drho_b = (xb == 0) ? a.drho_in : a.drho_out;
   float eq_b[9], eq_n[9];
   equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, eps_b, eq_b);

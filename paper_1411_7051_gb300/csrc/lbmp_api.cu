@@ -102,6 +102,7 @@ void release(lbmp_ctx *c) {
   cudaFree(c->buf[0]);
   cudaFree(c->buf[1]);
   cudaFree(c->med);
+  cudaFree(c->kn0);
   cudaFree(c->uprev);
   cudaFree(c->partials);
   cudaFree(c->results);
@@ -250,7 +251,17 @@ lbmp_status lbmp::validate_params(lbmp_params *p) {
       return fail(LBMP_EINVAL, "fp16_log2_scale must be in [-60, 60]");
     if (p->kernel != LBMP_KERNEL_AUTO && p->kernel != LBMP_KERNEL_STAGED && p->kernel != LBMP_KERNEL_DIRECT)
       return fail(LBMP_EINVAL, "kernel must be LBMP_KERNEL_AUTO, _STAGED or _DIRECT");
-    if (p->reserved != 0) return fail(LBMP_EINVAL, "reserved must be 0");
+    if (p->kn_model != LBMP_KN_BKC && p->kn_model != LBMP_KN_FIRST_ORDER)
+      return fail(LBMP_EINVAL, "kn_model must be LBMP_KN_BKC or LBMP_KN_FIRST_ORDER");
+    if (!std::isfinite(p->kn_beta)) return fail(LBMP_EINVAL, "kn_beta must be finite");
+    if (p->kn_beta != 0.0) {
+      if (p->kernel == LBMP_KERNEL_STAGED)
+        return fail(LBMP_EINVAL, "a dynamic Kn (kn_beta != 0) needs the direct kernel");
+      if (p->bc_x == LBMP_BCX_PRESSURE &&
+          !(1.0 + p->kn_beta * (p->rho_in - p->rho0) > 0.0 &&
+            1.0 + p->kn_beta * (p->rho_out - p->rho0) > 0.0))
+        return fail(LBMP_EINVAL, "kn_beta gives a non-positive pressure at rho_in or rho_out");
+    }
     if (p->fp16_rounding != LBMP_ROUND_STOCHASTIC && p->fp16_rounding != LBMP_ROUND_NEAREST)
       return fail(LBMP_EINVAL, "fp16_rounding must be LBMP_ROUND_STOCHASTIC or LBMP_ROUND_NEAREST");
 
@@ -264,6 +275,57 @@ const char *lbmp_last_error(void) { return g_err.c_str(); }
 double lbmp_fc(double kn) {
   if (!(kn >= 0.0)) return NAN;
   return lbmp::fc_bkc(kn);
+}
+
+double lbmp_fc_model(int32_t kn_model, double kn) {
+  if (!(kn >= 0.0) || (kn_model != LBMP_KN_BKC && kn_model != LBMP_KN_FIRST_ORDER)) return NAN;
+  return lbmp::fc_model(kn, kn_model);
+}
+
+double lbmp_kozeny_carman(double eps, double d) {
+  if (!(eps >= 0.0 && eps < 1.0) || !(d >= 0.0)) return NAN;
+  return d * d / 180.0 * eps * eps * eps / ((1.0 - eps) * (1.0 - eps));
+}
+
+double lbmp_mean_free_path(double mu, double p, double T, double M) {
+  if (!(mu > 0.0 && p > 0.0 && T > 0.0 && M > 0.0)) return NAN;
+  const double R = 8.314462618;  // J / (mol K)
+  return (mu / p) * std::sqrt(M_PI * R * T / (2.0 * M));
+}
+
+double lbmp_pore_radius(double k_d, double eps) {
+  if (!(k_d >= 0.0) || !(eps > 0.0)) return NAN;
+  const double mD = 9.869e-16;   // m^2
+  return 8.886e-2 * std::sqrt(k_d / mD / eps) * 1e-6;
+}
+
+lbmp_status lbmp_physical_medium(int64_t n, const double *eps, const double *d, double lambda,
+                                 double dx, double *k_i, double *kn) {
+  if (n < 0 || (n > 0 && (!eps || !d || !k_i || !kn)))
+    return fail(LBMP_EINVAL, "lbmp_physical_medium: NULL argument or n < 0");
+  if (!(lambda >= 0.0) || !(dx > 0.0) || !std::isfinite(lambda) || !std::isfinite(dx))
+    return fail(LBMP_EINVAL, "lbmp_physical_medium: lambda must be >= 0 and dx > 0");
+  for (int64_t i = 0; i < n; ++i) {
+    const double e = eps[i];
+    if (!(e >= 0.0 && e <= 1.0))
+      return fail(LBMP_EINVAL, "lbmp_physical_medium: eps[%lld] outside [0, 1]", (long long)i);
+    if (e == 0.0) {  // impermeable: k_i unused
+      k_i[i] = 1.0;
+      kn[i] = 0.0;
+      continue;
+    }
+    if (e == 1.0) {  // open pore: no medium, no slip correction
+      k_i[i] = INFINITY;
+      kn[i] = 0.0;
+      continue;
+    }
+    if (!(d[i] > 0.0) || !std::isfinite(d[i]))
+      return fail(LBMP_EINVAL, "lbmp_physical_medium: d[%lld] must be > 0", (long long)i);
+    const double kd = lbmp_kozeny_carman(e, d[i]);  // Eq. 9
+    k_i[i] = kd / (dx * dx);
+    kn[i] = lambda / lbmp_pore_radius(kd, e);       // Eq. 10-11: Kn = lambda / r
+  }
+  return LBMP_OK;
 }
 
 lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
@@ -289,7 +351,8 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     // FP32: the direct kernel already saturates HBM (the staged one reaches
     // ~0.95 of it); FP16: the staged kernel issues fewer instructions per node.
     c->staged = p.kernel == LBMP_KERNEL_STAGED ||
-                (p.kernel == LBMP_KERNEL_AUTO && p.storage == LBMP_STORE_FP16);
+                (p.kernel == LBMP_KERNEL_AUTO && p.storage == LBMP_STORE_FP16 &&
+                 p.kn_beta == 0.0);
     e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {
       delete c;
@@ -329,6 +392,8 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     LBMP_TRY(dalloc(c, &c->buf[0], c->buf_bytes(), "population buffer A"));
     LBMP_TRY(dalloc(c, &c->buf[1], c->buf_bytes(), "population buffer B"));
     LBMP_TRY(dalloc(c, (void **)&c->med, (size_t)c->plane * sizeof(float2), "medium"));
+    if (p.kn_beta != 0.0)
+      LBMP_TRY(dalloc(c, (void **)&c->kn0, (size_t)c->plane * sizeof(float), "Kn at p0"));
     LBMP_TRY(dalloc(c, (void **)&c->uprev, (size_t)c->plane * sizeof(float2), "velocity snapshot"));
     LBMP_TRY(dalloc(c, (void **)&c->partials,
                     (size_t)c->partials_blocks * lbmp::kNQ * sizeof(double), "reduction partials"));
@@ -381,8 +446,20 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
     }
     LBMP_CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
     LBMP_CK(cudaMemsetAsync(c->med, 0, (size_t)c->plane * sizeof(float2), c->stream));
-    LBMP_CK(lbmp::launch_medium(de, dk, dn, p.nx, p.ny, c->pitch, c->y_lo, c->y_hi, c->med,
-                                c->d_flag, c->partials, c->stream));
+    // with a dynamic Kn the largest k_a (FP16 scale) is that at the lowest
+    // imposed pressure
+    double kn_scale_max = 1.0;
+    if (c->kn0) {
+      LBMP_CK(cudaMemsetAsync(c->kn0, 0, (size_t)c->plane * sizeof(float), c->stream));
+      double qmin = 1.0;
+      if (p.bc_x == LBMP_BCX_PRESSURE)
+        qmin = std::min({1.0, 1.0 + p.kn_beta * (p.rho_in - p.rho0),
+                         1.0 + p.kn_beta * (p.rho_out - p.rho0)});
+      kn_scale_max = 1.0 / qmin;
+    }
+    LBMP_CK(lbmp::launch_medium(de, dk, dn, p.nx, p.ny, c->pitch, c->y_lo, c->y_hi, p.kn_model,
+                                c->kn0, kn_scale_max, c->med, c->d_flag, c->partials,
+                                c->stream));
     c->launches++;
     LBMP_CK(lbmp::launch_finalize(c->partials, lbmp::medium_blocks(p.nx, p.ny), lbmp::kNQ,
                                   c->results, c->stream, lbmp::kMediumMaxMask));
@@ -702,8 +779,9 @@ lbmp_status lbmp_get_info(lbmp_ctx *c, lbmp_info *out) {
   out->storage = c->p.storage;
   out->fluid_nodes = c->fluid_nodes;
   out->steps = c->steps;
-  // nine populations read and written once, plus the float2 medium
-  out->bytes_per_update = 2.0 * 9.0 * (double)c->elem + 8.0;
+  // nine populations read and written once, plus the float2 medium (and
+  // the Kn plane of a dynamic Kn)
+  out->bytes_per_update = 2.0 * 9.0 * (double)c->elem + 8.0 + (c->kn0 ? 4.0 : 0.0);
   out->fp16_scale = c->scale;
   out->eps_mean = c->eps_mean;
   out->device_bytes = c->device_bytes;

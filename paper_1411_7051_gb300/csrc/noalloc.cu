@@ -50,8 +50,8 @@ lbmp_status nfail(lbmp_status st, const char *fmt, ...) {
 
 struct NoallocArgs {
   int nx, ny;
-  int walls, pressure, forch;
-  double nu, Gx, Gy, rho0, rho_in, rho_out;
+  int walls, pressure, forch, kn_model;
+  double nu, Gx, Gy, rho0, rho_in, rho_out, kn_beta;
 };
 
 __global__ void __launch_bounds__(kNoallocBX)
@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(kNoallocBX)
     const double e = eps[j];
     double ux = 0.0;
     if (e > 0.0) {
-      const double ka = k_i[j] * lbmp::fc_bkc(kn[j]);
+      // Eq. 3; with a dynamic Kn at the node's pressure p0 (1 + beta (rho - rho0))
+      const double K = a.kn_beta == 0.0 ? kn[j] : kn[j] / (1.0 + a.kn_beta * (rho - a.rho0));
+      const double ka = k_i[j] * lbmp::fc_model(K, a.kn_model);
       const double inv_k = isinf(ka) ? 0.0 : 1.0 / ka;
       const double vx = mx / rho + 0.5 * e * a.Gx, vy = my / rho + 0.5 * e * a.Gy;
       const double c0 = 0.5 * (1.0 + 0.5 * e * a.nu * inv_k);
@@ -185,6 +187,8 @@ lbmp_status lbmp_permeability_noalloc(const lbmp_params *p, const double *f, con
     a.walls = walls;
     a.pressure = pressure;
     a.forch = p->forchheimer != 0;
+    a.kn_model = p->kn_model == LBMP_KN_FIRST_ORDER ? LBMP_KN_FIRST_ORDER : LBMP_KN_BKC;
+    a.kn_beta = p->kn_beta;
     const double J = (p->J == 0.0) ? 1.0 : p->J;
     a.nu = (p->tau - 0.5) / 3.0 / J;
     a.Gx = p->Gx;

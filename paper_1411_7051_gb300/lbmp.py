@@ -25,6 +25,7 @@ BCY_PERIODIC, BCY_WALLS = 0, 1
 STORE_FP32, STORE_FP16 = 0, 1
 ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
 KERNEL_AUTO, KERNEL_STAGED, KERNEL_DIRECT = 0, 1, 2
+KN_BKC, KN_FIRST_ORDER = 0, 1
 HOST, DEVICE = 0, 1
 
 _STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE",
@@ -47,8 +48,9 @@ class Params(ctypes.Structure):
         ("rho0", ctypes.c_double), ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
         ("forchheimer", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("fp16_log2_scale", ctypes.c_int32), ("fp16_rounding", ctypes.c_int32),
-        ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("kernel", ctypes.c_int32), ("kn_model", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+        ("kn_beta", ctypes.c_double),
     ]
 
 
@@ -99,6 +101,16 @@ def load(path: str = LIB_PATH):
     L.lbmp_last_error.argtypes = []
     L.lbmp_fc.restype = ctypes.c_double
     L.lbmp_fc.argtypes = [ctypes.c_double]
+    L.lbmp_fc_model.restype = ctypes.c_double
+    L.lbmp_fc_model.argtypes = [ctypes.c_int32, ctypes.c_double]
+    for name, nargs in (("lbmp_kozeny_carman", 2), ("lbmp_mean_free_path", 4),
+                        ("lbmp_pore_radius", 2)):
+        fn = getattr(L, name)
+        fn.restype = ctypes.c_double
+        fn.argtypes = [ctypes.c_double] * nargs
+    L.lbmp_physical_medium.restype = st
+    L.lbmp_physical_medium.argtypes = [ctypes.c_int64, _VP, _VP, ctypes.c_double,
+                                       ctypes.c_double, _VP, _VP]
     L.lbmp_create.restype = st
     L.lbmp_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_VP)]
     L.lbmp_destroy.restype = st
@@ -168,6 +180,41 @@ def fc(kn: float) -> float:
     return float(load().lbmp_fc(float(kn)))
 
 
+def fc_model(kn_model: int, kn: float) -> float:
+    """f_c of Eq. 6-7 (KN_BKC) or Eq. 4-5 (KN_FIRST_ORDER), library host code."""
+    return float(load().lbmp_fc_model(int(kn_model), float(kn)))
+
+
+def kozeny_carman(eps: float, d: float) -> float:
+    """Eq. 9: intrinsic permeability [m^2] of packed spheres of diameter d [m]."""
+    return float(load().lbmp_kozeny_carman(float(eps), float(d)))
+
+
+def mean_free_path(mu: float, p: float, T: float, M: float) -> float:
+    """Eq. 10: mean free path [m] (mu [Pa s], p [Pa], T [K], M [kg/mol])."""
+    return float(load().lbmp_mean_free_path(float(mu), float(p), float(T), float(M)))
+
+
+def pore_radius(k_d: float, eps: float) -> float:
+    """Eq. 11: characteristic pore radius [m] from k_d [m^2]."""
+    return float(load().lbmp_pore_radius(float(k_d), float(eps)))
+
+
+def physical_medium(eps, d, mean_free_path_m: float, dx: float):
+    """``lbmp_physical_medium``: lattice k_i and Kn fields (for set_fields)
+    of a medium given by porosity ``eps`` and grain diameter ``d`` [m] per
+    node (``d`` may be a scalar), gas mean free path [m] and node spacing
+    ``dx`` [m].  Returns (k_i, kn) as float64 arrays of eps's shape."""
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    dd = np.ascontiguousarray(np.broadcast_to(np.asarray(d, dtype=np.float64), e.shape))
+    k_i = np.empty_like(e)
+    kn = np.empty_like(e)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(load().lbmp_physical_medium(e.size, vp(e), vp(dd), float(mean_free_path_m),
+                                       float(dx), vp(k_i), vp(kn)))
+    return k_i, kn
+
+
 def permeability_noalloc(cfg: "SimConfig", f, eps, k_i, kn, out, stream=None):
     """``lbmp_permeability_noalloc``: k_g, <u_x> and the non-finite count of
     a state held in caller device memory, written to ``out`` (3 float64 on
@@ -211,14 +258,16 @@ class SimConfig:
     fp16_rounding: int = ROUND_STOCHASTIC
     kernel: int = KERNEL_AUTO
     seed: int = 0
+    kn_model: int = KN_BKC
+    kn_beta: float = 0.0
 
     def to_params(self, stream: int | None) -> Params:
         return Params(int(self.nx), int(self.ny), float(self.tau), float(self.J),
                       float(self.G[0]), float(self.G[1]), int(self.bc_x), int(self.bc_y),
                       float(self.rho0), float(self.rho_in), float(self.rho_out),
                       int(self.forchheimer), int(self.storage), int(self.fp16_log2_scale),
-                      int(self.fp16_rounding), int(self.kernel), 0,
-                      int(self.seed) & (2**64 - 1), stream)
+                      int(self.fp16_rounding), int(self.kernel), int(self.kn_model),
+                      int(self.seed) & (2**64 - 1), stream, float(self.kn_beta))
 
 
 class Sim:

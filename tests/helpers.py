@@ -22,6 +22,8 @@ class Case:
     rho_out: float = 1.0
     forchheimer: int = 0
     medium: media.Medium | None = None
+    kn_model: int = 0        # f_c: 0 Eq. 6-7, 1 Eq. 4-5
+    kn_beta: float = 0.0     # dynamic Kn (0: static)
 
 
 def oracle_sim(orc, case: Case):
@@ -29,7 +31,8 @@ def oracle_sim(orc, case: Case):
                         bc_x=orc.BC_PRESSURE if case.pressure else orc.BC_PERIODIC,
                         bc_y=orc.BC_WALLS if case.walls else orc.BC_PERIODIC,
                         rho_in=case.rho_in, rho_out=case.rho_out,
-                        forchheimer=case.forchheimer)
+                        forchheimer=case.forchheimer, kn_model=case.kn_model,
+                        kn_beta=case.kn_beta)
     s = orc.OracleSim(p)
     m = case.medium
     s.set_fields(m.eps, m.k_i, m.kn)
@@ -45,7 +48,8 @@ def gpu_sim(case: Case, storage: int = 0, fp16_log2_scale: int = 0, fp16_roundin
                          rho_in=case.rho_in, rho_out=case.rho_out,
                          forchheimer=case.forchheimer, storage=storage,
                          fp16_log2_scale=fp16_log2_scale, fp16_rounding=fp16_rounding,
-                         seed=seed, kernel=kernel)
+                         seed=seed, kernel=kernel, kn_model=case.kn_model,
+                         kn_beta=case.kn_beta)
     s = lbmp.Sim(cfg)
     m = case.medium
     s.set_fields(m.eps, m.k_i, m.kn)

@@ -56,6 +56,11 @@ def _create(L, **kw):
     ({"storage": 5}, "storage"),
     ({"fp16_log2_scale": 100}, "fp16_log2_scale"),
     ({"fp16_rounding": 3}, "fp16_rounding"),
+    ({"kn_model": 2}, "kn_model"),
+    ({"kn_beta": float("nan")}, "kn_beta"),
+    ({"kn_beta": 10.0, "kernel": lbmp.KERNEL_STAGED}, "direct kernel"),
+    ({"kn_beta": 1000.0, "bc_x": lbmp.BCX_PRESSURE, "rho_in": 1.0, "rho_out": 0.998},
+     "non-positive pressure"),
 ])
 def test_create_rejects_bad_parameters(L, kw, needle):
     st, msg = _create(L, **kw)

@@ -18,7 +18,7 @@ EX = [0, 1, 0, -1, 0, 1, -1, -1, 1]
 EY = [0, 0, 1, 0, -1, 1, 1, -1, -1]
 
 
-def _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=0):
+def _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=0, kn_beta=0.0):
     import torch
     ny, nx = med.eps.shape
     rng = np.random.default_rng(seed)
@@ -43,6 +43,14 @@ def _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=0):
                              bc_y=orc.BC_WALLS if cfg.bc_y else orc.BC_PERIODIC,
                              rho_in=cfg.rho_in, rho_out=cfg.rho_out,
                              forchheimer=cfg.forchheimer)
+
+    def ka_of(f, sy, sx):
+        """k_a of a source node: static, or with a dynamic Kn at the pressure
+        of its own post-stream state f (p / p0 = 1 + beta (rho - rho0))."""
+        if kn_beta == 0.0:
+            return ka[sy, sx]
+        q = 1.0 + kn_beta * (float(np.sum(f)) - 1.0)
+        return med.k_i[sy, sx] * orc.fc(med.kn[sy, sx] / q)
     exp = np.zeros_like(got)
     opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
     for n in range(nsamp):
@@ -50,13 +58,13 @@ def _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=0):
             sy = ys[n] - EY[i]
             if cfg.bc_y == lbmp.BCY_WALLS and sy in (0, ny - 1):
                 post = orc.collide_node(patch[:, n, 1, 1], med.eps[ys[n], xs[n]],
-                                        ka[ys[n], xs[n]], params)
+                                        ka_of(patch[:, n, 1, 1], ys[n], xs[n]), params)
                 exp[n, i] = post[opp[i]]
                 continue
             sy %= ny
             sx = xs[n] - EX[i]
-            post = orc.collide_node(patch[:, n, 1 - EY[i], 1 - EX[i]], med.eps[sy, sx],
-                                    ka[sy, sx], params)
+            src = patch[:, n, 1 - EY[i], 1 - EX[i]]
+            post = orc.collide_node(src, med.eps[sy, sx], ka_of(src, sy, sx), params)
             exp[n, i] = post[i]
     _, _, w = orc.lattice()
     dev = np.abs(exp - w[None, :])
@@ -67,19 +75,22 @@ def _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=0):
         assert np.all(err <= dev * 2.0 ** -10 + 1e-10), (err / (dev + 1e-30)).max()
 
 
-@pytest.mark.parametrize("storage", [lbmp.STORE_FP32, lbmp.STORE_FP16])
-def test_bench_workload_sampled_step(orc, storage):
+@pytest.mark.parametrize("storage,dynamic", [(lbmp.STORE_FP32, False), (lbmp.STORE_FP16, False),
+                                             (lbmp.STORE_FP32, True)])
+def test_bench_workload_sampled_step(orc, storage, dynamic):
     """The bench workload (4096^2 fractured shale, pressure x, periodic y,
-    Forchheimer), AUTO kernel selection as timed by bench.py."""
+    Forchheimer), AUTO kernel selection as timed by bench.py; also its
+    dynamic-Kn variant (inlet pressure twice the outlet one)."""
     import bench
     med, c = bench.workload(4096)
+    beta = bench.kn_beta_for(c) if dynamic else 0.0
     cfg = lbmp.SimConfig(c["nx"], c["ny"], tau=c["tau"], bc_x=c["bc_x"], bc_y=c["bc_y"],
                          rho_in=c["rho_in"], rho_out=c["rho_out"], forchheimer=c["forchheimer"],
-                         storage=storage)
+                         storage=storage, kn_beta=beta)
     with lbmp.Sim(cfg) as sim:
         sim.set_fields(med.eps, med.k_i, med.kn)
         sim.step(64)   # two graph replays: the timed path
-        _sampled_one_step(orc, sim, cfg, med, storage)
+        _sampled_one_step(orc, sim, cfg, med, storage, kn_beta=beta)
         kg, _ = sim.permeability()
         assert np.isfinite(kg)
 
