@@ -562,3 +562,45 @@ int orc_kg_fd(const orc_params *p, const double *eps, const double *k_i,
   free(kg);
   return failed ? -1 : 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Normalised velocity magnitude u0 = |u| / max |u| over every node of  */
+/* the fluid rows (Section IV.B, Fig. 6), counted in nbins equal ranges */
+/* of [0, 1] (u0 = 1 falls in the last one; max |u| = 0 puts every node */
+/* in the first).  *umax receives max |u|.                              */
+/* ------------------------------------------------------------------ */
+void orc_velocity_histogram(const orc_sim *s, int nbins, int64_t *counts, double *umax) {
+  const orc_params *p = &s->p;
+  const int64_t n = (int64_t)p->nx * p->ny;
+  double *speed = (double *)malloc((size_t)n * sizeof(double));
+  double mx = 0.0;
+  for (int k = 0; k < nbins; ++k) counts[k] = 0;
+  if (!speed) {
+    *umax = NAN;
+    return;
+  }
+  for (int y = 0; y < p->ny; ++y) {
+    if (orc_is_wall_row(p, y)) continue;
+    for (int x = 0; x < p->nx; ++x) {
+      const int64_t j = (int64_t)y * p->nx + x;
+      double u[2];
+      orc_node_state(s->f + j * 9, s->eps[j], orc_node_ka(s, j, s->f + j * 9), p, NULL, u, NULL);
+      speed[j] = sqrt(u[0] * u[0] + u[1] * u[1]);
+      if (speed[j] > mx) mx = speed[j];
+    }
+  }
+  for (int y = 0; y < p->ny; ++y) {
+    if (orc_is_wall_row(p, y)) continue;
+    for (int x = 0; x < p->nx; ++x) {
+      const int64_t j = (int64_t)y * p->nx + x;
+      int k = 0;
+      if (mx > 0.0) {
+        k = (int)floor(speed[j] / mx * nbins);
+        if (k > nbins - 1) k = nbins - 1;
+      }
+      counts[k]++;
+    }
+  }
+  free(speed);
+  *umax = mx;
+}

@@ -99,6 +99,8 @@ def _load(path: str):
     L.orc_residual.restype = ctypes.c_double
     L.orc_residual.argtypes = [ctypes.c_void_p, _D, _D]
     L.orc_lattice.argtypes = [_I, _I, _D]
+    L.orc_velocity_histogram.argtypes = [ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int64), _D]
     L.orc_kg_fd.restype = ctypes.c_int
     L.orc_kg_fd.argtypes = [P, _D, _D, _D, ctypes.c_int64, ctypes.c_double,
                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.c_int, _D]
@@ -323,6 +325,16 @@ class OracleSim:
         um = ctypes.c_double()
         kg = self._L.orc_permeability(self._h, ctypes.byref(um))
         return kg, um.value
+
+    def velocity_histogram(self, nbins: int = 10):
+        """Fig. 6: counts of u0 = |u| / max |u| in nbins equal ranges over the
+        nodes of the fluid rows, and max |u|."""
+        counts = np.zeros(nbins, dtype=np.int64)
+        umax = ctypes.c_double()
+        self._L.orc_velocity_histogram(self._h, int(nbins),
+                                       counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       ctypes.byref(umax))
+        return counts, umax.value
 
     def driving_force(self) -> float:
         """Body force plus the imposed pressure gradient (Darcy's law driver)."""

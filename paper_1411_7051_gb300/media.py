@@ -152,3 +152,70 @@ def random_populations(nx: int, ny: int, seed: int, base, amp: float = 1e-3) -> 
     rng = _rng(seed)
     base = np.asarray(base, dtype=np.float64).reshape(9, 1, 1)
     return base * (1.0 + amp * rng.uniform(-1, 1, size=(9, ny, nx)))
+
+
+PORE, IMPERMEABLE, PERMEABLE = 0, 1, 2
+
+
+def trimodal(nx: int = 410, ny: int = 200, seed: int = 4, frac_solid: float = 0.4,
+             frac_perm: float = 0.3, r_range=(4.0, 12.0), core_prob: float = 0.004,
+             grow_axis: float = 0.02, grow_diag: float = 0.005) -> np.ndarray:
+    """Labels of a three-component medium like that of Section IV.B (Fig. 4):
+    PORE, IMPERMEABLE solid, PERMEABLE solid, as int8 [ny][nx].
+
+    Impermeable solids: overlapping discs of radius U(r_range) with uniform
+    centres (periodic wrap) until they cover frac_solid of the lattice.
+    Permeable solids: quartet structure generation set (QSGS) in the space
+    left: each free cell becomes a growth core with probability core_prob;
+    then, sweep after sweep, every free cell next to a permeable one turns
+    permeable with probability grow_axis per axial and grow_diag per
+    diagonal permeable neighbour, until frac_perm of the lattice is
+    permeable (the last sweep keeps a random subset of its new cells).
+    The paper's own generators are not published; these are seeded
+    stand-ins with its volume fractions."""
+    rng = _rng(seed)
+    lab = np.full((ny, nx), PORE, dtype=np.int8)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    target = frac_solid * nx * ny
+    while np.count_nonzero(lab == IMPERMEABLE) < target:
+        cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
+        r = rng.uniform(*r_range)
+        dx = (xx - cx + nx / 2) % nx - nx / 2
+        dy = (yy - cy + ny / 2) % ny - ny / 2
+        lab[dx * dx + dy * dy <= r * r] = IMPERMEABLE
+    free = lab == PORE
+    lab[free & (rng.uniform(size=lab.shape) < core_prob)] = PERMEABLE
+    need = int(round(frac_perm * nx * ny))
+    dirs = [((0, 1), grow_axis), ((0, -1), grow_axis), ((1, 0), grow_axis), ((-1, 0), grow_axis),
+            ((1, 1), grow_diag), ((1, -1), grow_diag), ((-1, 1), grow_diag),
+            ((-1, -1), grow_diag)]
+    while True:
+        perm = lab == PERMEABLE
+        left = need - int(np.count_nonzero(perm))
+        if left <= 0 or not np.any(lab == PORE):
+            break
+        new = np.zeros_like(perm)
+        for (sy, sx), pr in dirs:
+            nb = np.roll(perm, (sy, sx), axis=(0, 1))
+            new |= nb & (lab == PORE) & (rng.uniform(size=lab.shape) < pr)
+        cand = np.flatnonzero(new)
+        if cand.size > left:
+            cand = rng.choice(cand, left, replace=False)
+        lab.flat[cand] = PERMEABLE
+    return lab
+
+
+def trimodal_medium(labels: np.ndarray, eps_ps: float, k_i_ps, kn_ps) -> Medium:
+    """Fields of a labelled three-component medium: pores eps = 1, k = inf
+    (no matrix), impermeable solids eps = 0 (k unused, set to 1), permeable
+    solids eps_ps with the given k_i and Kn (scalars or [ny][nx] arrays
+    read at the permeable cells)."""
+    shp = labels.shape
+    perm = labels == PERMEABLE
+    eps = np.where(labels == PORE, 1.0, 0.0)
+    eps[perm] = eps_ps
+    k_i = np.where(labels == PORE, np.inf, 1.0)
+    k_i[perm] = np.broadcast_to(np.asarray(k_i_ps, dtype=np.float64), shp)[perm]
+    kn = np.zeros(shp)
+    kn[perm] = np.broadcast_to(np.asarray(kn_ps, dtype=np.float64), shp)[perm]
+    return Medium(eps, k_i, kn, "trimodal")
