@@ -176,6 +176,19 @@ lbmp_status lbmp_set_populations(lbmp_ctx *ctx, const double *f, int32_t where);
  * Errors: ENAN (a non-finite velocity), ECUDA. */
 lbmp_status lbmp_permeability(lbmp_ctx *ctx, double *k_g, double *u_mean);
 
+/* Normalised velocity magnitude (Section IV.B, Fig. 6): u0 = |u| / max |u|
+ * over every node of the fluid rows (impermeable nodes count with u = 0),
+ * counted in nbins equal ranges of [0, 1]: counts[k] (host, nbins int64)
+ * holds the nodes with min(floor(u0 nbins), nbins - 1) = k, so u0 = 1 falls
+ * in the last range; max |u| = 0 puts every node in counts[0].  |u| =
+ * sqrt(ux^2 + uy^2) in FP64 from the FP32 velocity lbmp_macroscopic
+ * reports, each operation rounded separately (no fused multiply-add), and
+ * u0 nbins likewise.  *umax (host, may be NULL) receives max |u|.
+ * 1 <= nbins <= 64.  Synchronous.  Errors: EINVAL, ESTATE, ENAN (a
+ * non-finite velocity), ECUDA. */
+lbmp_status lbmp_velocity_histogram(lbmp_ctx *ctx, int32_t nbins, double *umax,
+                                    int64_t *counts);
+
 /* Relative velocity residual ||u - u_prev||_2 / ||u||_2 over fluid nodes,
  * u_prev being the velocity at the previous lbmp_residual call (zero after
  * set_fields); then stores u as the new u_prev.  FP64.  Synchronous. */

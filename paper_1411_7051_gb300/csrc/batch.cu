@@ -503,8 +503,12 @@ lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32
       a.rho0 = (float)p.rho0;
       a.drho_in = (float)(p.rho_in - p.rho0);
       a.drho_out = (float)(p.rho_out - p.rho0);
-      a.omega = (float)(1.0 / p.tau);
-      a.one_m_omega = (float)(1.0 - 1.0 / p.tau);
+      // omega on the grid of multiples of 2^-24 and 1 - omega formed from it:
+      // the two then sum to exactly 1 in FP32, so the collision conserves mass
+      // and momentum without a per-step (1 + O(2^-24)) factor that would
+      // compound over a run (the grid changes 1/tau by at most 2^-25)
+      a.omega = (float)(std::nearbyint(std::ldexp(1.0 / p.tau, 24)) * std::ldexp(1.0, -24));
+      a.one_m_omega = 1.0f - a.omega;
       a.cforce = (float)(1.0 - 0.5 / p.tau);
       a.nu = (float)((p.tau - 0.5) / 3.0 / p.J);
       a.Gx = (float)p.Gx;

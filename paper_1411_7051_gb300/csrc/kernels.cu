@@ -292,6 +292,106 @@ cudaError_t launch_finalize(const double *partials, int nblocks, int nq, double 
   return cudaGetLastError();
 }
 
+// ------------------------------------------- normalised-velocity histogram
+// |u| of node (x, y) in FP64 from the FP32 velocity of node_state (as the
+// macroscopic kernel reports it), every operation rounded separately so
+// that the bin decisions can be replayed exactly on the host.
+template <class S, bool DYN>
+__device__ __forceinline__ double node_speed(const typename S::T *__restrict__ fin,
+                                             const float2 *__restrict__ med, const StepArgs &a,
+                                             int x, int y) {
+  float d[9];
+  const long long jp = (long long)y * a.pitch + x;
+  const float2 m = med[jp];
+  pull_node<S>(fin, a, x, y, d);
+  if (a.pressure && (x == 0 || x == a.nx - 1)) pressure_node<S, DYN>(fin, med, a, x, y, m.x, d);
+  const NodeState s = node_state<DYN>(d, m.x, m.y, a, DYN ? a.kn0[jp] : 0.0f);
+  const double ux = s.ux, uy = s.uy;
+  return __dsqrt_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)));
+}
+
+// Pass 1: block maxima of |u| over the fluid rows into partials[block].
+template <class S, bool DYN>
+__global__ void __launch_bounds__(kMacroBX)
+    speed_max_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
+                     const float2 *__restrict__ med, double *__restrict__ partials) {
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * kMacroBX + threadIdx.x;
+  double v = 0.0;
+  if (x < a.nx && !(a.walls && (y == 0 || y == a.ny - 1))) v = node_speed<S, DYN>(fin, med, a, x, y);
+  if (!(v >= 0.0)) v = INFINITY;  // a non-finite speed poisons the maximum
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+  __shared__ double red[kMacroBX / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kMacroBX / 32; ++w) t = fmax(t, red[w]);
+    partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Pass 2: bin k = min(floor(|u| / umax * nbins), nbins - 1) (0 if umax is
+// 0), counted per block in shared memory, then added to counts.
+template <class S, bool DYN>
+__global__ void __launch_bounds__(kMacroBX)
+    histogram_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
+                     const float2 *__restrict__ med, double umax, int nbins,
+                     unsigned long long *__restrict__ counts) {
+  __shared__ unsigned sh[kMaxHistBins];
+  for (int k = threadIdx.x; k < nbins; k += kMacroBX) sh[k] = 0u;
+  __syncthreads();
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * kMacroBX + threadIdx.x;
+  if (x < a.nx && !(a.walls && (y == 0 || y == a.ny - 1))) {
+    int k = 0;
+    if (umax > 0.0) {
+      const double u0 = __ddiv_rn(node_speed<S, DYN>(fin, med, a, x, y), umax);
+      const double f = floor(__dmul_rn(u0, (double)nbins));
+      k = f >= (double)(nbins - 1) ? nbins - 1 : (int)f;
+    }
+    atomicAdd(&sh[k], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nbins; k += kMacroBX)
+    if (sh[k]) atomicAdd(counts + k, (unsigned long long)sh[k]);
+}
+
+cudaError_t launch_speed_max(int storage, const StepArgs &a, const void *fin, const float2 *med,
+                             double *partials, cudaStream_t s) {
+  dim3 block(kMacroBX);
+  dim3 grid((a.nx + kMacroBX - 1) / kMacroBX, a.ny);
+  const bool dyn = a.kn0 != nullptr;
+  if (storage == 0) {
+    if (dyn) speed_max_kernel<StoreF32, true><<<grid, block, 0, s>>>(a, (const float *)fin, med, partials);
+    else speed_max_kernel<StoreF32, false><<<grid, block, 0, s>>>(a, (const float *)fin, med, partials);
+  } else {
+    if (dyn) speed_max_kernel<StoreF16, true><<<grid, block, 0, s>>>(a, (const __half *)fin, med, partials);
+    else speed_max_kernel<StoreF16, false><<<grid, block, 0, s>>>(a, (const __half *)fin, med, partials);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_histogram(int storage, const StepArgs &a, const void *fin, const float2 *med,
+                             double umax, int nbins, unsigned long long *counts, cudaStream_t s) {
+  dim3 block(kMacroBX);
+  dim3 grid((a.nx + kMacroBX - 1) / kMacroBX, a.ny);
+  const bool dyn = a.kn0 != nullptr;
+  if (storage == 0) {
+    if (dyn)
+      histogram_kernel<StoreF32, true><<<grid, block, 0, s>>>(a, (const float *)fin, med, umax, nbins, counts);
+    else
+      histogram_kernel<StoreF32, false><<<grid, block, 0, s>>>(a, (const float *)fin, med, umax, nbins, counts);
+  } else {
+    if (dyn)
+      histogram_kernel<StoreF16, true><<<grid, block, 0, s>>>(a, (const __half *)fin, med, umax, nbins, counts);
+    else
+      histogram_kernel<StoreF16, false><<<grid, block, 0, s>>>(a, (const __half *)fin, med, umax, nbins, counts);
+  }
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- medium
 __global__ void __launch_bounds__(kMediumBX)
     medium_kernel(const double *__restrict__ eps, const double *__restrict__ k_i,

@@ -82,6 +82,16 @@ cudaError_t launch_medium(const double *eps, const double *k_i, const double *kn
                           float *kn0, double kn_scale_max, float2 *med, unsigned *bad,
                           double *partials, cudaStream_t s);
 
+// Normalised-velocity histogram: pass 1 writes the maximum of |u| over the
+// fluid rows of each macro block (macro_blocks(a) doubles, a.y0 ignored);
+// pass 2 adds the counts of bins min(floor(|u| / umax * nbins), nbins - 1)
+// to counts[0..nbins).  nbins <= kMaxHistBins.
+constexpr int kMaxHistBins = 64;
+cudaError_t launch_speed_max(int storage, const StepArgs &a, const void *fin, const float2 *med,
+                             double *partials, cudaStream_t s);
+cudaError_t launch_histogram(int storage, const StepArgs &a, const void *fin, const float2 *med,
+                             double umax, int nbins, unsigned long long *counts, cudaStream_t s);
+
 // Inverse of the pull: write a post-collision buffer whose pull gives the
 // post-stream populations f ([9][ny][nx] float64).
 cudaError_t launch_load_pops(int storage, const StepArgs &a, int rows, const double *f,

@@ -188,6 +188,7 @@ struct NodeState {
   float rho;     // physical density
   float ux, uy;  // physical velocity (Eq. 17 / quadratic form)
   float Fx, Fy;  // total force (Eq. 2 / Eq. 8)
+  float rFx, rFy;  // rho S F (stored units): the momentum the force adds
   float ieps;    // 1 / eps (0 for an impermeable node)
 };
 
@@ -235,12 +236,20 @@ __device__ __forceinline__ NodeState node_state(const float d[9], float eps, flo
     s.uy = vy * idn;
     s.Fx = fmaf(-drag, s.ux, eGx);
     s.Fy = fmaf(-drag, s.uy, eGy);
+    const float rs = s.rho * a.scale;
+    s.rFx = rs * s.Fx;
+    s.rFy = rs * s.Fy;
   } else {
     s.ieps = 0.0f;
     s.ux = 0.0f;
     s.uy = 0.0f;
     s.Fx = -2.0f * mx * c;
     s.Fy = -2.0f * my * c;
+    // rho F = -2 m exactly: the collision then reverses the momentum of an
+    // impermeable node exactly (a rounded rho * (1 / rho) would make it
+    // grow or decay by ~1e-7 per step, compounding over the run)
+    s.rFx = -2.0f * mx;
+    s.rFy = -2.0f * my;
   }
   return s;
 }
@@ -279,8 +288,8 @@ __device__ __forceinline__ void collide(float d[9], const NodeState &s, const St
   const float usq = 1.5f * ie * fmaf(ux, ux, uy * uy);
   const float uF3 = 3.0f * ie * fmaf(ux, Fx, uy * Fy);
   const float A = fmaf(om, s.drho_s, -rs * fmaf(om, usq, cf * uF3));
-  const float Px = 3.0f * fmaf(om, mx, rs * Fx);
-  const float Py = 3.0f * fmaf(om, my, rs * Fy);
+  const float Px = 3.0f * fmaf(om, mx, s.rFx);
+  const float Py = 3.0f * fmaf(om, my, s.rFy);
   const float qq = om * 4.5f * ie * rs;
   const float gg = cf * 9.0f * ie * rs;
   const float Mxx = ux * fmaf(qq, ux, gg * Fx);

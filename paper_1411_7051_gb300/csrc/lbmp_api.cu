@@ -109,6 +109,7 @@ void release(lbmp_ctx *c) {
   cudaFree(c->d_flag);
   cudaFree(c->d_tctr);
   cudaFree(c->d_err);
+  cudaFree(c->d_hist);
   if (c->h_results) cudaFreeHost(c->h_results);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -668,6 +669,50 @@ lbmp_status lbmp_permeability(lbmp_ctx *c, double *k_g, double *u_mean) {
     return LBMP_OK;
   } catch (...) {
     return fail(LBMP_ECUDA, "lbmp_permeability: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_velocity_histogram(lbmp_ctx *c, int32_t nbins, double *umax,
+                                    int64_t *counts) {
+  try {
+    if (!c || !counts) return fail(LBMP_EINVAL, "lbmp_velocity_histogram: NULL argument");
+    if (nbins < 1 || nbins > lbmp::kMaxHistBins)
+      return fail(LBMP_EINVAL, "nbins must be in [1, %d]", lbmp::kMaxHistBins);
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_velocity_histogram: no fields set");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    if (!c->d_hist) {
+      st = dalloc(c, (void **)&c->d_hist, lbmp::kMaxHistBins * sizeof(unsigned long long),
+                  "histogram counts");
+      if (st) return st;
+    }
+    StepArgs a = c->args();
+    a.y0 = 0;
+    LBMP_CK(lbmp::launch_speed_max(c->p.storage, a, c->buf[c->cur], c->med, c->partials,
+                                   c->stream));
+    LBMP_CK(lbmp::launch_finalize(c->partials, lbmp::macro_blocks(a), 1, c->results, c->stream,
+                                  1u));
+    LBMP_CK(cudaMemcpyAsync(c->h_results, c->results, sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+    LBMP_CK(cudaStreamSynchronize(c->stream));
+    const double um = c->h_results[0];
+    if (!std::isfinite(um)) return fail(LBMP_ENAN, "a fluid node has a non-finite velocity");
+    LBMP_CK(cudaMemsetAsync(c->d_hist, 0, lbmp::kMaxHistBins * sizeof(unsigned long long),
+                            c->stream));
+    LBMP_CK(lbmp::launch_histogram(c->p.storage, a, c->buf[c->cur], c->med, um, nbins, c->d_hist,
+                                   c->stream));
+    c->launches += 3;
+    unsigned long long h[lbmp::kMaxHistBins];
+    LBMP_CK(cudaMemcpyAsync(h, c->d_hist, (size_t)nbins * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, c->stream));
+    LBMP_CK(cudaStreamSynchronize(c->stream));
+    st = check_err(c);
+    if (st) return st;
+    for (int k = 0; k < nbins; ++k) counts[k] = (int64_t)h[k];
+    if (umax) *umax = um;
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_velocity_histogram: unexpected exception");
   }
 }
 

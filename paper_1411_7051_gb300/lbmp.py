@@ -129,6 +129,8 @@ def load(path: str = LIB_PATH):
     L.lbmp_set_populations.argtypes = [_VP, _VP, ctypes.c_int32]
     L.lbmp_permeability.restype = st
     L.lbmp_permeability.argtypes = [_VP, _D, _D]
+    L.lbmp_velocity_histogram.restype = st
+    L.lbmp_velocity_histogram.argtypes = [_VP, ctypes.c_int32, _D, ctypes.POINTER(ctypes.c_int64)]
     L.lbmp_residual.restype = st
     L.lbmp_residual.argtypes = [_VP, _D]
     L.lbmp_mass.restype = st
@@ -371,6 +373,15 @@ class Sim:
         kg, um = ctypes.c_double(), ctypes.c_double()
         _check(load().lbmp_permeability(self._h, ctypes.byref(kg), ctypes.byref(um)))
         return kg.value, um.value
+
+    def velocity_histogram(self, nbins: int = 10):
+        """``lbmp_velocity_histogram`` (Fig. 6): node counts of u0 = |u| /
+        max |u| in nbins equal ranges, and max |u|."""
+        counts = np.zeros(int(nbins), dtype=np.int64)
+        um = ctypes.c_double()
+        _check(load().lbmp_velocity_histogram(self._h, int(nbins), ctypes.byref(um),
+                                              counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return counts, um.value
 
     def residual(self) -> float:
         r = ctypes.c_double()
