@@ -67,6 +67,8 @@ typedef int32_t lbmp_status;
                                 storage, staged for FP16 */
 #define LBMP_KERNEL_STAGED 1 /* bulk copies into a shared-memory ring (persistent) */
 #define LBMP_KERNEL_DIRECT 2 /* one-pass loads from global memory */
+#define LBMP_KERNEL_WIDE 3   /* FP16 storage only: four consecutive nodes per thread,
+                                8-byte loads and stores per plane */
 
 #define LBMP_HOST 0
 #define LBMP_DEVICE 1

@@ -497,7 +497,7 @@ lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32
       const int walls = p.bc_y == LBMP_BCY_WALLS;
       a.nx = nx[i];
       a.ny = ny[i];
-      a.pitch = ((nx[i] + 63) / 64) * 64;
+      a.pitch = lbmp::row_pitch(nx[i]);
       a.y0 = walls ? 1 : 0;
       a.plane = (long long)a.pitch * ny[i];
       a.rho0 = (float)p.rho0;

@@ -35,7 +35,8 @@ struct lbmp_ctx {
   unsigned long long *d_tctr = nullptr;  // time level for the stochastic rounding
   unsigned *d_err = nullptr;             // raised by a bounded wait that gave up
   int nsm = 1;                           // SMs of the device
-  bool staged = true;
+  bool staged = true;            // staged kernel (else direct or wide)
+  bool wide = false;             // wide FP16 kernel
   bool sr = false;
   bool fields_set = false;
   int64_t steps = 0;

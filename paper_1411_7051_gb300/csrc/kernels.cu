@@ -14,6 +14,7 @@
 #include "kernels.h"
 #include "lattice.cuh"
 #include "staged.cuh"
+#include "wide.cuh"
 
 namespace lbmp {
 
@@ -105,6 +106,26 @@ cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const
   return cudaGetLastError();
 }
 
+// -------------------------------------------------------- wide variant
+cudaError_t launch_wide(bool sr, const StepArgs &a, int rows, const void *fin, void *fout,
+                        const float2 *med, const unsigned long long *tctr, int k,
+                        cudaStream_t s) {
+  if (rows <= 0 || a.nx <= 0) return cudaSuccess;
+  dim3 block(kWideBX);
+  dim3 grid((a.nx + kWideBX * kWideV - 1) / (kWideBX * kWideV), rows);
+  const __half *i = (const __half *)fin;
+  __half *o = (__half *)fout;
+  const bool dyn = a.kn0 != nullptr;
+  if (sr) {
+    if (dyn) wide_step_kernel<true, true><<<grid, block, 0, s>>>(a, i, o, med, tctr, k);
+    else wide_step_kernel<true, false><<<grid, block, 0, s>>>(a, i, o, med, tctr, k);
+  } else {
+    if (dyn) wide_step_kernel<false, true><<<grid, block, 0, s>>>(a, i, o, med, tctr, k);
+    else wide_step_kernel<false, false><<<grid, block, 0, s>>>(a, i, o, med, tctr, k);
+  }
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------ staged variant
 template <class S, bool SR>
 static cudaError_t launch_staged_t(const StepArgs &a, int rows, const void *fin, void *fout,
@@ -112,7 +133,8 @@ static cudaError_t launch_staged_t(const StepArgs &a, int rows, const void *fin,
                                    unsigned *err, int nsm, cudaStream_t s) {
   using C = StageCfg<S>;
   using L = StageLayout<S>;
-  const int ntiles = ((a.nx + C::W - 1) / C::W) * ((rows + C::H - 1) / C::H);
+  const long long span = (long long)rows * a.pitch;  // flat nodes of the launch rows
+  const int ntiles = (int)((span + C::W - 1) / C::W);
   const int grid = ntiles < nsm ? ntiles : nsm;
   staged_step_kernel<S, SR><<<grid, kStagedThreads, L::kSmemBytes, s>>>(
       a, (const typename S::T *)fin, (typename S::T *)fout, med, tctr, k, rows, err);

@@ -37,10 +37,29 @@ __host__ __device__ inline double fc_model(double kn, int model) {
   return model == 1 ? 1.0 + 4.0 * kn : fc_bkc(kn);
 }
 
+// Row pitch (elements) of the device planes of a lattice nx wide: nx
+// rounded up to kPitchAlign, plus kPitchSkew when that is a multiple of
+// kPitchSkewEvery.  Row strides that are multiples of large powers of two
+// (4096 FP16 nodes = 8 KiB) make the concurrent tile copies of the staged
+// kernel alias in the DRAM channels: 89 GLUPS at 4096^2 FP16 against 124
+// with the skew (and 86 -> 107 at 2048^2, 90 -> 128 at 6144^2).
+constexpr int kPitchAlign = 64;
+constexpr int kPitchSkewEvery = 512;
+constexpr int kPitchSkew = 64;
+inline int row_pitch(int nx) {
+  int p = ((nx + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+  if (p % kPitchSkewEvery == 0) p += kPitchSkew;
+  return p;
+}
+
 // One time step over rows [a.y0, a.y0 + rows).  sr: FP16 stochastic
 // rounding with the bits of time level *tctr + k.
 cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
                         void *fout, const float2 *med, const unsigned long long *tctr, int k,
+                        cudaStream_t s);
+// Vectorised FP16 variant of the same step (four nodes per thread).
+cudaError_t launch_wide(bool sr, const StepArgs &a, int rows, const void *fin, void *fout,
+                        const float2 *med, const unsigned long long *tctr, int k,
                         cudaStream_t s);
 // Staged variant of the same step (asynchronous bulk copies into a shared-
 // memory ring, persistent grid of at most nsm CTAs); a bounded wait that

@@ -51,7 +51,6 @@ lbmp_status cuda_fail(cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);      \
   } while (0)
 
-constexpr int kPitchAlign = 64;   // elements: 256 B rows for FP32, 128 B for FP16
 constexpr int kGraphSteps = 32;   // even, so a replay keeps the buffer parity
 constexpr uint64_t kStateMagic = 0x4c424d5053544131ull;  // "LBMPSTA1"
 
@@ -166,6 +165,7 @@ lbmp_status run_macro(lbmp_ctx *c, lbmp::MacroOut o, bool reduce) {
 // One step kernel launch (the variant the context selected).
 cudaError_t launch_one(lbmp_ctx *c, const StepArgs &a, const void *fin, void *fout, int k,
                        cudaStream_t s) {
+  if (c->wide) return lbmp::launch_wide(c->sr, a, c->rows(), fin, fout, c->med, c->d_tctr, k, s);
   if (c->staged)
     return lbmp::launch_staged(c->p.storage, c->sr, a, c->rows(), fin, fout, c->med, c->d_tctr,
                                k, c->d_err, c->nsm, s);
@@ -250,8 +250,11 @@ lbmp_status lbmp::validate_params(lbmp_params *p) {
       return fail(LBMP_EINVAL, "storage must be LBMP_STORE_FP32 or LBMP_STORE_FP16");
     if (p->fp16_log2_scale < -60 || p->fp16_log2_scale > 60)
       return fail(LBMP_EINVAL, "fp16_log2_scale must be in [-60, 60]");
-    if (p->kernel != LBMP_KERNEL_AUTO && p->kernel != LBMP_KERNEL_STAGED && p->kernel != LBMP_KERNEL_DIRECT)
-      return fail(LBMP_EINVAL, "kernel must be LBMP_KERNEL_AUTO, _STAGED or _DIRECT");
+    if (p->kernel != LBMP_KERNEL_AUTO && p->kernel != LBMP_KERNEL_STAGED &&
+        p->kernel != LBMP_KERNEL_DIRECT && p->kernel != LBMP_KERNEL_WIDE)
+      return fail(LBMP_EINVAL, "kernel must be LBMP_KERNEL_AUTO, _STAGED, _DIRECT or _WIDE");
+    if (p->kernel == LBMP_KERNEL_WIDE && p->storage != LBMP_STORE_FP16)
+      return fail(LBMP_EINVAL, "the wide kernel needs FP16 storage");
     if (p->kn_model != LBMP_KN_BKC && p->kn_model != LBMP_KN_FIRST_ORDER)
       return fail(LBMP_EINVAL, "kn_model must be LBMP_KN_BKC or LBMP_KN_FIRST_ORDER");
     if (!std::isfinite(p->kn_beta)) return fail(LBMP_EINVAL, "kn_beta must be finite");
@@ -354,6 +357,7 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     c->staged = p.kernel == LBMP_KERNEL_STAGED ||
                 (p.kernel == LBMP_KERNEL_AUTO && p.storage == LBMP_STORE_FP16 &&
                  p.kn_beta == 0.0);
+    c->wide = p.kernel == LBMP_KERNEL_WIDE;
     e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {
       delete c;
@@ -364,7 +368,7 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
       delete c;
       return cuda_fail(e, "shared-memory limit of the staged kernel");
     }
-    c->pitch = ((p.nx + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+    c->pitch = lbmp::row_pitch(p.nx);
     c->plane = (long long)c->pitch * p.ny;
     c->y_lo = (p.bc_y == LBMP_BCY_WALLS) ? 1 : 0;
     c->y_hi = (p.bc_y == LBMP_BCY_WALLS) ? p.ny - 1 : p.ny;

@@ -9,13 +9,16 @@
 // cp.async.bulk (completion counted on an mbarrier), while 24 consumer
 // warps pull, collide and store from the stage that has landed.
 //
-// Tile: H rows x W nodes.  A stage holds, for each plane i and tile row r,
-// the source row y - e_iy over columns [x_a - A, x_a + W + A) (A = 16 bytes
-// of halo on each side, so every copy starts and ends on a 16-byte
-// boundary), and the medium of the tile.  Sources that the stage cannot
-// hold -- the periodic wrap of column 0 / nx-1 and the bounce-back of the
-// rows next to a plate -- are read from global memory by the few threads
-// that need them.
+// Tile: W consecutive nodes of the padded lattice taken row after row (flat
+// index y * pitch + x), so a tile may continue on the next row and no tile
+// is left partly empty at a row end.  A stage holds, for each plane i, the
+// sources of the tile's nodes, flat [T - e_iy pitch - A, T - e_iy pitch + W
+// + A) (A = 16 bytes of halo on each side, so every copy starts and ends on
+// a 16-byte boundary): one contiguous span, split where it wraps around the
+// plane (the periodic edge in y).  Interior nodes never read across a row
+// end.  Sources that the stage cannot hold -- the periodic wrap of column
+// 0 / nx-1 and the bounce-back of the rows next to a plate -- are read from
+// global memory by the few threads that need them.
 //
 // Every wait is bounded (kWaitNs of %globaltimer); a wait that gives up
 // raises *err and the CTA returns (the host reports LBMP_ETIMEOUT).
@@ -58,6 +61,8 @@ struct StageLayout {
   static_assert(C::A * (int)sizeof(T) == 16, "halo of 16 bytes");
   static_assert(2 * C::STAGES * 8 <= kBarBytes, "barrier area");
   static_assert((C::H * C::W / 2) % (kConsumerWarps * 32) == 0, "node pairs per consumer thread");
+  static_assert(C::H == 1, "tiles are spans of the flattened lattice");
+  static_assert(C::W % 64 == 0, "tile starts stay 16-byte aligned");
   static_assert(C::W % 2 == 0 && C::A % 2 == 0, "pairs stay aligned");
 };
 
@@ -113,17 +118,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 }
 
 // --------------------------------------------------------------- helpers
-// Source row of plane i for target row y: y - e_iy (periodic wrap), or -1
-// when it is a plate row (the target then bounces back).
-__device__ __forceinline__ int staged_src_row(const StepArgs &a, int i, int y) {
-  const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-  int ys = y - ey;
-  if (a.walls && (ys == 0 || ys == a.ny - 1) && ey != 0) return -1;
-  if (ys < 0) ys += a.ny;
-  if (ys >= a.ny) ys -= a.ny;
-  return ys;
-}
-
 // Post-stream values of node (x, y) at tile position (r, c), stored units.
 template <class S>
 __device__ __forceinline__ void pull_staged(const typename S::T *__restrict__ sp,
@@ -204,16 +198,22 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int tiles_x = (a.nx + W - 1) / W;
-  const int tiles_y = (rows + H - 1) / H;
-  const int ntiles = tiles_x * tiles_y;
+  // Tiles are W consecutive nodes of the padded lattice read row after row
+  // (flat index y * pitch + x over the launch rows), so no tile is partly
+  // empty at a row end.  The source of plane i for flat index p is
+  // p - e_iy * pitch (mod ny * pitch, the periodic wrap in y): the sources of
+  // a tile are one contiguous span per plane, split only where it wraps.
+  const long long F0 = (long long)a.y0 * a.pitch;
+  const long long Fend = (long long)(a.y0 + rows) * a.pitch;
+  const long long NP = (long long)a.ny * a.pitch;
+  const int ntiles = (int)((Fend - F0 + W - 1) / W);
   const int y_end = a.y0 + rows;
 
   if (warp == kConsumerWarps) {
     // ------------------------------------------------------- producer
-    // The copies of a tile (9 planes x H rows, then H medium rows) are
-    // spread over the lanes of this warp, which issue them concurrently
+    // Lane i < 9 copies plane i (one or a few segments), lane 9 the medium,
     // after lane 0 has posted the expected byte count.
+    constexpr uint32_t kPlaneBytes = (uint32_t)(RW * sizeof(T));
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
@@ -230,37 +230,30 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
             mbar_wait(full((it - j) % NS), (uint32_t)((it - j) / NS) & 1u, err);
         return;
       }
-      const int ya = a.y0 + (t / tiles_x) * H;
-      const int xa = (t % tiles_x) * W;
-      const int nrow = min(H, y_end - ya);
-      const int gx0 = max(xa - A, 0), gx1 = min(xa + W + A, a.pitch);
-      const uint32_t row_bytes = (uint32_t)(gx1 - gx0) * (uint32_t)sizeof(T);
-      const int scol = gx0 - (xa - A);
-      const uint32_t med_bytes = (uint32_t)(min(xa + W, a.pitch) - xa) * 8u;
-      const int ncopy = 10 * nrow;  // copy j < 9 nrow: plane j / nrow, row j % nrow
-      if (lane == 0) {
-        uint32_t total = (uint32_t)nrow * med_bytes;
-        for (int i = 0; i < 9; ++i)
-          for (int r = 0; r < nrow; ++r)
-            if (staged_src_row(a, i, ya + r) >= 0) total += row_bytes;
-        mbar_arrive_expect_tx(full(s), total);
-      }
+      const long long T0 = F0 + (long long)t * W;
+      const uint32_t med_bytes = (uint32_t)(min((long long)W, Fend - T0) * 8);
+      if (lane == 0) mbar_arrive_expect_tx(full(s), 9u * kPlaneBytes + med_bytes);
       __syncwarp();
       if (t == a.test_drop_tile) continue;  // the consumers' wait must run out
       const uint32_t st = sbase + (uint32_t)L::kBarBytes + (uint32_t)s * (uint32_t)L::kStageBytes;
-      for (int j = lane; j < ncopy; j += 32) {
-        if (j < 9 * nrow) {
-          const int i = j / nrow, r = j % nrow;
-          const int ys = staged_src_row(a, i, ya + r);
-          if (ys < 0) continue;
-          const uint32_t dst = st + (uint32_t)(((i * H + r) * RW + scol) * (int)sizeof(T));
-          const T *src = fin + (long long)i * a.plane + (long long)ys * a.pitch + gx0;
-          bulk_g2s(dst, src, row_bytes, full(s));
-        } else {
-          const int r = j - 9 * nrow;
-          const uint32_t dst = st + (uint32_t)L::kPopBytes + (uint32_t)(r * W * 8);
-          bulk_g2s(dst, med + (long long)(ya + r) * a.pitch + xa, med_bytes, full(s));
+      if (lane < 9) {
+        const int ey = (lane == 2 || lane == 5 || lane == 6) ? 1
+                       : ((lane == 4 || lane == 7 || lane == 8) ? -1 : 0);
+        long long v = T0 - (long long)ey * a.pitch - A;
+        while (v < 0) v += NP;
+        while (v >= NP) v -= NP;
+        const T *plane = fin + (long long)lane * a.plane;
+        uint32_t dst = st + (uint32_t)lane * kPlaneBytes;
+        long long left = RW;
+        while (left > 0) {
+          const long long seg = min(left, NP - v);
+          bulk_g2s(dst, plane + v, (uint32_t)(seg * (long long)sizeof(T)), full(s));
+          dst += (uint32_t)(seg * (long long)sizeof(T));
+          left -= seg;
+          v = 0;
         }
+      } else if (lane == 9) {
+        bulk_g2s(st + (uint32_t)L::kPopBytes, med + T0, med_bytes, full(s));
       }
     }
     return;
@@ -274,22 +267,28 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   }
   // Each consumer thread owns node pairs (x0, x0 + 1), x0 even, of the tile.
   constexpr int kPairs = (H * W / 2) / (kConsumerWarps * 32);
+  // first node of this block's first tile, and the step between its tiles
+  const long long Tb = F0 + (long long)blockIdx.x * W;
+  int yT = (int)(Tb / a.pitch), xT = (int)(Tb - (long long)yT * a.pitch);
+  const long long D = (long long)gridDim.x * W;
+  const int dy = (int)(D / a.pitch), dx = (int)(D - (long long)dy * a.pitch);
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
     const int s = it % NS;
     if (!mbar_wait(full(s), (uint32_t)(it / NS) & 1u, err)) return;
-    const int ya = a.y0 + (t / tiles_x) * H;
-    const int xa = (t % tiles_x) * W;
-    const int nrow = min(H, y_end - ya);
     const unsigned char *sb = smem + L::kBarBytes + s * L::kStageBytes;
     const T *sp = reinterpret_cast<const T *>(sb);
     const float2 *sm = reinterpret_cast<const float2 *>(sb + L::kPopBytes);
 #pragma unroll 1
     for (int j = 0; j < kPairs; ++j) {
       const int q = threadIdx.x + j * kConsumerWarps * 32;  // pair index in the tile
-      const int r = (2 * q) / W, c = (2 * q) % W;
-      const int x = xa + c, y = ya + r;
-      if (r >= nrow || x >= a.nx) continue;
+      const int r = 0, c = 2 * q;
+      int x = xT + c, y = yT;
+      while (x >= a.pitch) {  // at most W / pitch + 1 rows per tile
+        x -= a.pitch;
+        ++y;
+      }
+      if (y >= y_end || x >= a.nx) continue;
       const bool two = x + 1 < a.nx;
       float dA[9], dB[9];
       const float4 m = *reinterpret_cast<const float4 *>(sm + r * W + c);
@@ -337,21 +336,28 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
       if (two) {
         const NodeState nB = node_state(dB, m.z, m.w, a);
         collide<S::kHiLo>(dB, nB, a);
-        const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
-        constexpr uint32_t kC[9] = {0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du, 0x27d4eb2fu,
-                                    0x165667b1u, 0xd3a2646du, 0xfd7046c5u, 0xb55a4f09u,
-                                    0x7feb352du};
-#pragma unroll
-        for (int i = 0; i < 9; ++i)  // 32 random bits per direction and pair
-          S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? h * kC[i] : 0u, 0u);
       } else {
-        const uint32_t h = SR ? mix32((uint32_t)o ^ ts) : 0u;
+        // a last node of an odd row is stored as a pair with a zero in the
+        // row padding (x = nx < pitch), drawing its rounding bits as a pair
 #pragma unroll
-        for (int i = 0; i < 9; ++i) S::template st1r<SR>(fout + i * a.plane + o, dA[i], h, i);
+        for (int i = 0; i < 9; ++i) dB[i] = 0.0f;
       }
+      const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
+      constexpr uint32_t kC[9] = {0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du, 0x27d4eb2fu,
+                                  0x165667b1u, 0xd3a2646du, 0xfd7046c5u, 0xb55a4f09u,
+                                  0x7feb352du};
+#pragma unroll
+      for (int i = 0; i < 9; ++i)  // 32 random bits per direction and pair
+        S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? h * kC[i] : 0u, 0u);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty(s));
+    xT += dx;
+    yT += dy;
+    if (xT >= a.pitch) {
+      xT -= a.pitch;
+      ++yT;
+    }
   }
 }
 

@@ -24,7 +24,7 @@ BCX_PERIODIC, BCX_PRESSURE = 0, 1
 BCY_PERIODIC, BCY_WALLS = 0, 1
 STORE_FP32, STORE_FP16 = 0, 1
 ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
-KERNEL_AUTO, KERNEL_STAGED, KERNEL_DIRECT = 0, 1, 2
+KERNEL_AUTO, KERNEL_STAGED, KERNEL_DIRECT, KERNEL_WIDE = 0, 1, 2, 3
 KN_BKC, KN_FIRST_ORDER = 0, 1
 HOST, DEVICE = 0, 1
 

@@ -1,10 +1,12 @@
 """Index arithmetic of the staged step kernel, replayed on the CPU (no GPU).
 
-The staged kernel copies row tiles with cp.async.bulk, which needs 16-byte
-aligned global and shared addresses and sizes, and must stay inside the
-population buffer and inside its shared-memory stage.  This test walks the
-producer's copy list and the consumers' shared-memory reads for many lattice
-shapes and boundary kinds and checks every range and alignment.  The tile
+The staged kernel copies spans of the flattened lattice with cp.async.bulk,
+which needs 16-byte aligned global and shared addresses and sizes, and must
+stay inside the population buffer and inside its shared-memory stage.  This
+test walks the producer's copy segments (with the wrap around the plane),
+the consumers' shared-memory reads and their incremental tile coordinates
+for many lattice shapes, boundary kinds and grid sizes, and checks every
+range and alignment.  The tile
 constants are read from the kernel header so the replay cannot drift."""
 import os
 import re
@@ -29,85 +31,99 @@ def stage_cfg():
 
 
 def pitch_of(nx):
-    text = open(os.path.join(CSRC, "lbmp_api.cu")).read()
+    text = open(os.path.join(CSRC, "kernels.h")).read()
     align = int(re.search(r"kPitchAlign = (\d+);", text).group(1))
-    return ((nx + align - 1) // align) * align
+    every = int(re.search(r"kPitchSkewEvery = (\d+);", text).group(1))
+    skew = int(re.search(r"kPitchSkew = (\d+);", text).group(1))
+    p = ((nx + align - 1) // align) * align
+    return p + skew if p % every == 0 else p
 
 
 EY = [0, 0, 1, 0, -1, 1, 1, -1, -1]
 
 
-def src_row(ny, walls, i, y):
-    ys = y - EY[i]
-    if walls and EY[i] != 0 and ys in (0, ny - 1):
-        return -1
-    return ys % ny
-
-
-def replay(nx, ny, walls, store):
+def replay(nx, ny, walls, store, grids=(1, 7, 152)):
     cfg, cw = stage_cfg()
     c = cfg[store]
     W, H, A, NS, elem = c["W"], c["H"], c["A"], c["NS"], c["elem"]
+    assert H == 1 and W % 64 == 0
     RW = W + 2 * A
-    pop_bytes = 9 * H * RW * elem
-    med_bytes_stage = H * W * 8
-    stage_bytes = pop_bytes + med_bytes_stage
+    pop_bytes = 9 * RW * elem
+    stage_bytes = pop_bytes + W * 8
     bar_bytes = 128
-    smem_bytes = bar_bytes + NS * stage_bytes
-    assert smem_bytes <= 227 * 1024
+    assert bar_bytes + NS * stage_bytes <= 227 * 1024
     assert 2 * NS * 8 <= bar_bytes
     pitch = pitch_of(nx)
-    plane = pitch * ny
+    NP = pitch * ny                      # nodes of a plane (the wrap length)
+    stride = NP                          # plane stride
     y0, rows = (1, ny - 2) if walls else (0, ny)
-    tiles_x = -(-nx // W)
-    tiles_y = -(-rows // H)
-    for t in range(tiles_x * tiles_y):
-        ya = y0 + (t // tiles_x) * H
-        xa = (t % tiles_x) * W
-        nrow = min(H, y0 + rows - ya)
-        assert nrow >= 1
-        gx0, gx1 = max(xa - A, 0), min(xa + W + A, pitch)
-        scol = gx0 - (xa - A)
-        row_bytes = (gx1 - gx0) * elem
-        med_bytes = (min(xa + W, pitch) - xa) * 8
-        total = nrow * med_bytes
-        for i in range(9):
-            for r in range(nrow):
-                ys = src_row(ny, walls, i, ya + r)
-                if ys < 0:
-                    continue
-                total += row_bytes
-                # shared destination inside row (i, r) of the stage, aligned
-                dst = ((i * H + r) * RW + scol) * elem
-                assert dst % 16 == 0 and row_bytes % 16 == 0 and row_bytes > 0
-                assert scol >= 0 and scol + (gx1 - gx0) <= RW
-                assert dst + row_bytes <= pop_bytes
-                # global source inside the plane row, aligned
-                src = (i * plane + ys * pitch + gx0) * elem
-                assert src % 16 == 0
-                assert 0 <= ys < ny and 0 <= gx0 < gx1 <= pitch
-        for r in range(nrow):
-            dst = pop_bytes + r * W * 8
-            assert dst % 16 == 0 and med_bytes % 16 == 0 and med_bytes <= W * 8
-            src = ((ya + r) * pitch + xa) * 8
-            assert src % 16 == 0 and (ya + r) < ny
+    F0, Fend = y0 * pitch, (y0 + rows) * pitch
+    ntiles = -(-(Fend - F0) // W)
+    for t in range(ntiles):
+        T0 = F0 + t * W
+        assert T0 < Fend
+        med_elems = min(W, Fend - T0)
+        total = 9 * RW * elem + med_elems * 8
         assert total < 2 ** 20  # mbarrier tx-count range
-        # consumer reads: row (i, r), column A + c - 1 .. A + c + 1 for the node
-        # and its pressure-neighbour (c - 1 .. c + 1)
-        for c in (-1, 0, 1, W - 2, W - 1, W):
+        for lane in range(9):
+            # producer lane `lane`: plane lane's sources, flat [T0 - e_y pitch - A, + RW) mod NP
+            v = T0 - EY[lane] * pitch - A
+            while v < 0:
+                v += NP
+            while v >= NP:
+                v -= NP
+            dst = lane * RW * elem
+            left = RW
+            virt = T0 - EY[lane] * pitch - A
+            while left > 0:
+                seg = min(left, NP - v)
+                assert seg > 0
+                src = (lane * stride + v) * elem
+                assert src % 16 == 0 and (seg * elem) % 16 == 0 and dst % 16 == 0
+                assert 0 <= v and v + seg <= NP
+                assert dst + seg * elem <= (lane + 1) * RW * elem
+                # every stage element holds plane[virtual index mod NP]
+                assert (virt + (dst // elem - lane * RW)) % NP == v
+                dst += seg * elem
+                left -= seg
+                v = 0
+            assert dst == (lane + 1) * RW * elem
+        # medium: [T0, T0 + med_elems) of the float2 plane, into the stage tail
+        assert (T0 * 8) % 16 == 0 and (med_elems * 8) % 16 == 0 and T0 + med_elems <= NP
+        assert pop_bytes % 16 == 0
+        # consumer reads of an interior node at tile offset cc: stage index
+        # A + cc + sh, which holds the flat source p - e_y pitch + sh
+        for cc in range(0, W, max(1, W // 97)):
+            p = T0 + cc
+            if p >= Fend:
+                break
+            x, y = p % pitch, p // pitch
+            if not (1 <= x <= nx - 2):
+                continue
             for sh in (-1, 0, 1):
-                col = A + c + sh
-                if c in (-1, W) and sh != 0:
-                    continue  # neighbours are only taken at c + 1 >= 0 or c - 1 <= W - 1
-                assert 0 <= col < RW
-    # consumer thread mapping covers each tile node exactly once
-    per = H * W // (cw * 32)
+                assert 0 <= A + cc + sh < RW
+                assert (p + sh) // pitch == y  # never across a row end
+    # consumers track the tile start (x, y) incrementally: same as the division
+    for g in grids:
+        g = min(g, ntiles)
+        for b in range(g):
+            Tb = F0 + b * W
+            yT, xT = divmod(Tb, pitch)
+            dy, dx = divmod(g * W, pitch)
+            for t in range(b, ntiles, g):
+                assert (yT, xT) == divmod(F0 + t * W, pitch)
+                xT += dx
+                yT += dy
+                if xT >= pitch:
+                    xT -= pitch
+                    yT += 1
+    # consumer thread mapping covers each tile node pair exactly once
+    per = W // 2 // (cw * 32)
     seen = set()
     for tid in range(cw * 32):
         for j in range(per):
-            q = tid + j * cw * 32
-            seen.add((q // W, q % W))
-    assert len(seen) == H * W
+            seen.add(2 * (tid + j * cw * 32))
+    assert seen == set(range(0, W, 2))
 
 
 @pytest.mark.parametrize("store", ["StoreF32", "StoreF16"])
