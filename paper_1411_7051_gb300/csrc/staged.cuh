@@ -174,6 +174,71 @@ __device__ __forceinline__ void pull_staged(const typename S::T *__restrict__ sp
   }
 }
 
+// The 32 random bits of direction i of a node pair (stochastic rounding).
+__device__ __forceinline__ uint32_t pair_bits(uint32_t h, int i) {
+  constexpr uint32_t kC[9] = {0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du, 0x27d4eb2fu, 0x165667b1u,
+                              0xd3a2646du, 0xfd7046c5u, 0xb55a4f09u, 0x7feb352du};
+  return h * kC[i];
+}
+
+// Pressure column xb (0 or nx - 1) at tile position c: non-equilibrium
+// extrapolation from the neighbouring interior node (stage position cn).
+template <class S>
+__device__ __forceinline__ void staged_pressure(const typename S::T *__restrict__ sp,
+                                                const typename S::T *__restrict__ fin,
+                                                const float2 *__restrict__ med, const StepArgs &a,
+                                                int cn, int xb, int y, float eps_b, float d[9]) {
+  const int xn = (xb == 0) ? 1 : a.nx - 2;
+  const float2 mn = med[(long long)y * a.pitch + xn];
+  float dn[9];
+  pull_staged<S>(sp, fin, a, 0, cn, xn, y, dn);
+  const NodeState sn = node_state(dn, mn.x, mn.y, a);
+  const float drho_b = (xb == 0) ? a.drho_in : a.drho_out;
+  float eq_b[9], eq_n[9];
+  equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, eps_b, eq_b);
+  equilibrium_dev(sn.drho_s * a.inv_scale, sn.rho, sn.ux, sn.uy, mn.x, eq_n);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) d[i] = fmaf(a.scale, eq_b[i] - eq_n[i], dn[i]);
+}
+
+// Update of a node pair that needs more than the stage holds: the periodic
+// wrap at x = 0 and nx - 1, the bounce-back next to a plate, the pressure
+// columns, the lone last node of an odd row.  These are a few pairs per
+// row; keeping them out of line keeps the interior path's registers and
+// code lean.  The step arguments come by value: taking the address of the
+// kernel parameter would move every read of it to local memory.
+template <class S, bool SR>
+__device__ __noinline__ void staged_edge_pair(const typename S::T *__restrict__ sp,
+                                              const typename S::T *__restrict__ fin,
+                                              typename S::T *__restrict__ fout,
+                                              const float2 *__restrict__ med, const StepArgs a,
+                                              int c, int x, int y, float4 m, uint32_t ts) {
+  const bool two = x + 1 < a.nx;
+  float dA[9], dB[9];
+  pull_staged<S>(sp, fin, a, 0, c, x, y, dA);
+  if (two) pull_staged<S>(sp, fin, a, 0, c + 1, x + 1, y, dB);
+  if (a.pressure) {
+    if (x == 0 || x == a.nx - 1) staged_pressure<S>(sp, fin, med, a, x == 0 ? c + 1 : c - 1, x, y, m.x, dA);
+    if (two && x + 1 == a.nx - 1) staged_pressure<S>(sp, fin, med, a, c, x + 1, y, m.z, dB);
+  }
+  const NodeState nA = node_state(dA, m.x, m.y, a);
+  collide<S::kHiLo>(dA, nA, a);
+  if (two) {
+    const NodeState nB = node_state(dB, m.z, m.w, a);
+    collide<S::kHiLo>(dB, nB, a);
+  } else {
+    // a last node of an odd row is stored as a pair with a zero in the row
+    // padding (x = nx < pitch), drawing its rounding bits as a pair
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dB[i] = 0.0f;
+  }
+  const long long o = (long long)y * a.pitch + x;
+  const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? pair_bits(h, i) : 0u, 0u);
+}
+
 // ------------------------------------------------------------------ kernel
 template <class S, bool SR>
 __global__ void __launch_bounds__(kStagedThreads, 1)
@@ -282,73 +347,40 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
 #pragma unroll 1
     for (int j = 0; j < kPairs; ++j) {
       const int q = threadIdx.x + j * kConsumerWarps * 32;  // pair index in the tile
-      const int r = 0, c = 2 * q;
+      const int c = 2 * q;
       int x = xT + c, y = yT;
       while (x >= a.pitch) {  // at most W / pitch + 1 rows per tile
         x -= a.pitch;
         ++y;
       }
       if (y >= y_end || x >= a.nx) continue;
-      const bool two = x + 1 < a.nx;
-      float dA[9], dB[9];
-      const float4 m = *reinterpret_cast<const float4 *>(sm + r * W + c);
-      const bool edge = x == 0 || x + 2 >= a.nx || (a.walls && (y == 1 || y == a.ny - 2));
-      if (!edge) {
-        // interior pair: e_x = 0 directions as one vector read per plane
-        const T *row = sp + r * RW + A + c;
-        constexpr int PL = H * RW;  // elements between planes in a stage
-        S::ld2(row, dA[0], dB[0]);
-        S::ld2(row + 2 * PL, dA[2], dB[2]);
-        S::ld2(row + 4 * PL, dA[4], dB[4]);
-        dA[1] = S::ld1(row + 1 * PL - 1); dB[1] = S::ld1(row + 1 * PL);
-        dA[5] = S::ld1(row + 5 * PL - 1); dB[5] = S::ld1(row + 5 * PL);
-        dA[8] = S::ld1(row + 8 * PL - 1); dB[8] = S::ld1(row + 8 * PL);
-        dA[3] = S::ld1(row + 3 * PL + 1); dB[3] = S::ld1(row + 3 * PL + 2);
-        dA[6] = S::ld1(row + 6 * PL + 1); dB[6] = S::ld1(row + 6 * PL + 2);
-        dA[7] = S::ld1(row + 7 * PL + 1); dB[7] = S::ld1(row + 7 * PL + 2);
-      } else {
-        pull_staged<S>(sp, fin, a, r, c, x, y, dA);
-        if (two) pull_staged<S>(sp, fin, a, r, c + 1, x + 1, y, dB);
-        if (a.pressure) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int xb = x + h;
-            if (!(xb == 0 || xb == a.nx - 1) || (h == 1 && !two)) continue;
-            float *d = h ? dB : dA;
-            const int cn = (xb == 0) ? c + h + 1 : c + h - 1;
-            const int xn = (xb == 0) ? 1 : a.nx - 2;
-            const float2 mn = med[(long long)y * a.pitch + xn];
-            float dn[9];
-            pull_staged<S>(sp, fin, a, r, cn, xn, y, dn);
-            const NodeState sn = node_state(dn, mn.x, mn.y, a);
-            const float drho_b = (xb == 0) ? a.drho_in : a.drho_out;
-            float eq_b[9], eq_n[9];
-            equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, h ? m.z : m.x, eq_b);
-            equilibrium_dev(sn.drho_s * a.inv_scale, sn.rho, sn.ux, sn.uy, mn.x, eq_n);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) d[i] = fmaf(a.scale, eq_b[i] - eq_n[i], dn[i]);
-          }
-        }
+      const float4 m = *reinterpret_cast<const float4 *>(sm + c);
+      if (x == 0 || x + 2 >= a.nx || (a.walls && (y == 1 || y == a.ny - 2))) {
+        staged_edge_pair<S, SR>(sp, fin, fout, med, a, c, x, y, m, ts);
+        continue;
       }
+      // interior pair: e_x = 0 directions as one vector read per plane
+      float dA[9], dB[9];
+      const T *row = sp + A + c;
+      constexpr int PL = RW;  // elements between planes in a stage
+      S::ld2(row, dA[0], dB[0]);
+      S::ld2(row + 2 * PL, dA[2], dB[2]);
+      S::ld2(row + 4 * PL, dA[4], dB[4]);
+      dA[1] = S::ld1(row + 1 * PL - 1); dB[1] = S::ld1(row + 1 * PL);
+      dA[5] = S::ld1(row + 5 * PL - 1); dB[5] = S::ld1(row + 5 * PL);
+      dA[8] = S::ld1(row + 8 * PL - 1); dB[8] = S::ld1(row + 8 * PL);
+      dA[3] = S::ld1(row + 3 * PL + 1); dB[3] = S::ld1(row + 3 * PL + 2);
+      dA[6] = S::ld1(row + 6 * PL + 1); dB[6] = S::ld1(row + 6 * PL + 2);
+      dA[7] = S::ld1(row + 7 * PL + 1); dB[7] = S::ld1(row + 7 * PL + 2);
       const NodeState nA = node_state(dA, m.x, m.y, a);
       collide<S::kHiLo>(dA, nA, a);
+      const NodeState nB = node_state(dB, m.z, m.w, a);
+      collide<S::kHiLo>(dB, nB, a);
       const long long o = (long long)y * a.pitch + x;
-      if (two) {
-        const NodeState nB = node_state(dB, m.z, m.w, a);
-        collide<S::kHiLo>(dB, nB, a);
-      } else {
-        // a last node of an odd row is stored as a pair with a zero in the
-        // row padding (x = nx < pitch), drawing its rounding bits as a pair
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dB[i] = 0.0f;
-      }
       const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
-      constexpr uint32_t kC[9] = {0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du, 0x27d4eb2fu,
-                                  0x165667b1u, 0xd3a2646du, 0xfd7046c5u, 0xb55a4f09u,
-                                  0x7feb352du};
 #pragma unroll
       for (int i = 0; i < 9; ++i)  // 32 random bits per direction and pair
-        S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? h * kC[i] : 0u, 0u);
+        S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? pair_bits(h, i) : 0u, 0u);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty(s));
