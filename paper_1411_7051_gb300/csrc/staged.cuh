@@ -4,9 +4,9 @@
 // The fused step moves every population once per time step, so it is
 // bound by HBM bandwidth, and bandwidth needs many bytes in flight.  Here
 // the bytes in flight do not depend on registers: a persistent CTA per SM
-// runs one producer lane that copies row tiles of the nine population
+// runs one producer warp that copies tile spans of the nine population
 // planes and of the medium into a ring of shared-memory stages with
-// cp.async.bulk (completion counted on an mbarrier), while 24 consumer
+// cp.async.bulk (completion counted on an mbarrier), while 16 consumer
 // warps pull, collide and store from the stage that has landed.
 //
 // Tile: W consecutive nodes of the padded lattice taken row after row (flat
@@ -31,7 +31,7 @@
 
 namespace lbmp {
 
-constexpr int kConsumerWarps = 24;
+constexpr int kConsumerWarps = 16;
 constexpr int kStagedThreads = (kConsumerWarps + 1) * 32;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
@@ -39,11 +39,11 @@ template <class S>
 struct StageCfg;
 template <>
 struct StageCfg<StoreF32> {
-  static constexpr int W = 1536, H = 1, A = 4, STAGES = 3;
+  static constexpr int W = 1024, H = 1, A = 4, STAGES = 4;
 };
 template <>
 struct StageCfg<StoreF16> {
-  static constexpr int W = 1536, H = 1, A = 8, STAGES = 5;
+  static constexpr int W = 2048, H = 1, A = 8, STAGES = 4;
 };
 
 template <class S>
