@@ -171,10 +171,11 @@ def test_two_component_fp32(orc, kn):
 
 
 def test_forchheimer_shale_fp32(orc):
-    """Fractured shale, transient.  Matrix velocities (k_i ~ 1e-6) are ~1e-9
-    under a density deviation of ~1e-3, so FP32 carries them with a few
-    significant digits only; the fracture velocities dominate the L2 norm.
-    Velocity bound 2e-5 (measured ~1.1e-5), permeability 1e-5."""
+    """Fractured shale, transient, tau 0.9.  Matrix velocities (k_i ~ 1e-6)
+    are ~1e-9 under a density deviation of ~1e-3, so FP32 carries them with
+    a few significant digits only; the fracture velocities dominate the L2
+    norm.  Velocity bound 1e-5 (measured 1.4e-6 with the collision's
+    1 - omega and omega summing to exactly 1), permeability 1e-5."""
     med = media.shale_fractures(n=160, seed=5, n_fractures=4, length=(40, 120))
     case = Case(160, 160, tau=0.9, pressure=True, walls=False, rho_in=1.001,
                 rho_out=0.999, forchheimer=1, medium=med)
@@ -182,7 +183,7 @@ def test_forchheimer_shale_fp32(orc):
     gs = gpu_sim(case, FP32)
     osim.step(600)
     gs.step(600)
-    _compare_velocity(gs, osim, case, rel_u=2e-5, rel_k=1e-5)
+    _compare_velocity(gs, osim, case, rel_u=1e-5, rel_k=1e-5)
 
 
 def test_impermeable_and_open_nodes_fp32(orc):
