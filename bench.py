@@ -615,7 +615,8 @@ def run_batch(args, ws, rank, local):
                        "instances": len(sizes), "nodes": nodes,
                        "storage": "fp16" if storage == lbmp.STORE_FP16 else "fp32",
                        "shape": [info.shape_threads, info.shape_nodes_per_thread,
-                                 "persistent" if info.persistent else "one block per item"],
+                                 {0: "one block per item", 1: "persistent",
+                                  2: "staged (bulk-copy tiles)"}[int(info.persistent)]],
                        "l2": "inputs larger than L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"of {kind}",

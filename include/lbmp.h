@@ -278,8 +278,9 @@ lbmp_status lbmp_permeability_gradient(lbmp_ctx *ctx, int64_t nsteps, int64_t ev
  * realizations x Knudsen numbers) share the physics parameters of p (tau, J,
  * G, boundary kinds, densities, Forchheimer, storage, rounding, seed; p->nx,
  * p->ny and p->kernel are ignored) and advance together: one launch per time
- * step covers a work list of row segments of all instances, either one block
- * per segment or a persistent grid walking it (CUDA graphs of 32 steps).  Each instance has its own populations, medium
+ * step covers a work list of row segments of all instances (one block per
+ * segment, or a persistent grid walking it), or the tiles of all instances
+ * in the staged bulk-copy kernel (CUDA graphs of 32 steps).  Each instance has its own populations, medium
  * and FP16 scale; the arithmetic per node is that of lbmp_step (Section III,
  * Eq. 12-17).  The launch shape (threads per block x nodes per thread x
  * grid mode) is chosen by lbmp_batch_tune.
@@ -290,7 +291,10 @@ typedef struct lbmp_batch_info {
   int32_t count;
   int32_t shape_threads;          /* launch shape in use */
   int32_t shape_nodes_per_thread;
-  int32_t persistent;             /* 1: persistent grid, 0: one block per work item */
+  int32_t persistent;             /* 0: one block per work item, 1: persistent grid,
+                                     2: staged kernel (bulk copies of tiles of W
+                                     nodes into shared memory; threads = consumer
+                                     threads, nodes per thread per tile) */
   int64_t total_nodes;            /* lattice updates per time step */
   int64_t steps;
   int64_t launches;
@@ -309,6 +313,8 @@ lbmp_status lbmp_batch_set_fields(lbmp_batch *b, int32_t i, const double *eps, c
                                   const double *kn, int32_t where);
 /* n time steps of every instance; ESTATE until every instance has fields. */
 lbmp_status lbmp_batch_step(lbmp_batch *b, int64_t n);
+/* Wait for the queued steps; ETIMEOUT if a bounded wait of the staged
+ * kernel gave up (the instances' state is then undefined). */
 lbmp_status lbmp_batch_synchronize(lbmp_batch *b);
 /* Global permeability and <u_x> of every instance (host arrays of count
  * doubles; either may be NULL), FP64 segmented reductions.  Synchronous. */
@@ -319,6 +325,10 @@ lbmp_status lbmp_batch_populations(lbmp_batch *b, int32_t i, double *f, int32_t 
  * batch, keep the fastest, restore the populations and time level.  Returns
  * the chosen candidate index and its time per step (either may be NULL). */
 lbmp_status lbmp_batch_tune(lbmp_batch *b, int32_t steps, int32_t *chosen, double *ms_per_step);
+/* Use launch candidate `shape` (0 <= shape < the number of candidates, as
+ * lbmp_batch_tune reports them; the last one is the staged bulk-copy
+ * kernel).  Errors: EINVAL. */
+lbmp_status lbmp_batch_set_shape(lbmp_batch *b, int32_t shape);
 lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out);
 
 /* Global permeability of a lattice state held entirely in caller memory,

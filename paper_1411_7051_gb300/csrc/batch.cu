@@ -7,8 +7,9 @@
 // (Section III) over a flat work list: work item w is a row segment of
 // BX * NPT nodes of instance item_inst[w].  Either one block per item, or a
 // persistent grid (SMs x resident blocks) walking contiguous item ranges.
-// The launch shape (BX, NPT, grid mode) is picked by lbmp_batch_tune, which
-// times every candidate on the batch itself and restores the populations.
+// The launch shape (BX, NPT, grid mode, or the staged bulk-copy kernel over
+// a tile list) is picked by lbmp_batch_tune, which times every candidate on
+// the batch itself and restores the populations.
 // Per-instance global permeabilities are FP64 segmented reductions.
 #include <cuda_runtime.h>
 
@@ -24,6 +25,7 @@
 #include "kernels.h"
 #include "lattice.cuh"
 #include "lbmp.h"
+#include "staged.cuh"
 
 namespace lbmp {
 
@@ -113,6 +115,153 @@ __global__ void __launch_bounds__(BX)
   }
 }
 
+// --------------------------------------------------- staged batched kernel
+// The staged step (staged.cuh) over the tiles of every instance: tile t is
+// W consecutive nodes of one instance's padded lattice, tiles[t] = (instance,
+// x and y of its first node, end of the instance's fluid rows).  The physics
+// shared by all instances comes in `base`; per tile the consumers override
+// the instance's geometry and FP16 scale, which then live in registers.
+template <class S, bool SR>
+__global__ void __launch_bounds__(kStagedThreads, 1)
+    batch_staged_kernel(const StepArgs base, const BatchInst *__restrict__ inst,
+                        const int4 *__restrict__ tiles, int ntiles, int parity,
+                        const unsigned long long *__restrict__ tctr, int k, unsigned *err) {
+  using L = StageLayout<S>;
+  using C = StageCfg<S>;
+  using T = typename S::T;
+  constexpr int W = C::W, A = C::A, NS = C::STAGES, RW = L::RW;
+  constexpr uint32_t kPlaneBytes = (uint32_t)(RW * sizeof(T));
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t sbase = smem_u32(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto full = [&](int s) { return sbase + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return sbase + 8u * (uint32_t)(NS + s); };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------- producer
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int s = it % NS;
+      const uint32_t use = (uint32_t)(it / NS);
+      if (use > 0) {
+        if (lane == 0) ok = mbar_wait(empty(s), (use - 1) & 1u, err);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
+      if (!ok) {
+        if (lane == 0)
+          for (int j = 1; j < NS && j <= it; ++j)
+            mbar_wait(full((it - j) % NS), (uint32_t)((it - j) / NS) & 1u, err);
+        return;
+      }
+      const int4 tr = tiles[t];
+      const BatchInst &I = inst[tr.x];
+      const int pitch = I.a.pitch;
+      const long long NP = (long long)I.a.ny * pitch;
+      const long long T0 = (long long)tr.z * pitch + tr.y;
+      const long long Fend = (long long)tr.w * pitch;
+      const uint32_t med_bytes = (uint32_t)(min((long long)W, Fend - T0) * 8);
+      if (lane == 0) mbar_arrive_expect_tx(full(s), 9u * kPlaneBytes + med_bytes);
+      __syncwarp();
+      const uint32_t st = sbase + (uint32_t)L::kBarBytes + (uint32_t)s * (uint32_t)L::kStageBytes;
+      if (lane < 9) {
+        const int ey = (lane == 2 || lane == 5 || lane == 6) ? 1
+                       : ((lane == 4 || lane == 7 || lane == 8) ? -1 : 0);
+        long long v = T0 - (long long)ey * pitch - A;
+        while (v < 0) v += NP;
+        while (v >= NP) v -= NP;
+        const T *plane = (const T *)I.buf[parity] + (long long)lane * I.a.plane;
+        uint32_t dst = st + (uint32_t)lane * kPlaneBytes;
+        long long left = RW;
+        while (left > 0) {
+          const long long seg = min(left, NP - v);
+          bulk_g2s(dst, plane + v, (uint32_t)(seg * (long long)sizeof(T)), full(s));
+          dst += (uint32_t)(seg * (long long)sizeof(T));
+          left -= seg;
+          v = 0;
+        }
+      } else if (lane == 9) {
+        bulk_g2s(st + (uint32_t)L::kPopBytes, I.med + T0, med_bytes, full(s));
+      }
+    }
+    return;
+  }
+  // --------------------------------------------------------- consumers
+  uint32_t ts = 0;
+  if (SR) {
+    const unsigned long long tl = *tctr + (unsigned long long)k;
+    ts = mix32((uint32_t)tl * 0x9e3779b9u ^ base.seed_lo ^ mix32((uint32_t)(tl >> 32) ^ base.seed_hi));
+  }
+  constexpr int kPairs = (W / 2) / (kConsumerWarps * 32);
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int s = it % NS;
+    if (!mbar_wait(full(s), (uint32_t)(it / NS) & 1u, err)) return;
+    const int4 tr = tiles[t];
+    const BatchInst &I = inst[tr.x];
+    const T *fin = (const T *)I.buf[parity];
+    T *fout = (T *)I.buf[parity ^ 1];
+    const float2 *med = I.med;
+    const unsigned char *sb = smem + L::kBarBytes + s * L::kStageBytes;
+    const T *sp = reinterpret_cast<const T *>(sb);
+    const float2 *sm = reinterpret_cast<const float2 *>(sb + L::kPopBytes);
+    StepArgs a = base;
+    a.nx = I.a.nx;
+    a.ny = I.a.ny;
+    a.pitch = I.a.pitch;
+    a.plane = I.a.plane;
+    a.scale = I.a.scale;
+    a.inv_scale = I.a.inv_scale;
+    const uint32_t tsi = SR ? ts ^ mix32((uint32_t)I.index * 0x85ebca77u + 1u) : 0u;
+#pragma unroll 1
+    for (int j = 0; j < kPairs; ++j) {
+      const int c = 2 * (threadIdx.x + j * kConsumerWarps * 32);
+      int x = tr.y + c, y = tr.z;
+      while (x >= a.pitch) {
+        x -= a.pitch;
+        ++y;
+      }
+      if (y >= tr.w || x >= a.nx) continue;
+      const float4 m = *reinterpret_cast<const float4 *>(sm + c);
+      if (x == 0 || x + 2 >= a.nx || (a.walls && (y == 1 || y == a.ny - 2))) {
+        staged_edge_pair<S, SR>(sp, fin, fout, med, a, c, x, y, m, tsi);
+        continue;
+      }
+      staged_interior_pair<S, SR>(sp, fout, a, c, x, y, m, tsi);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty(s));
+  }
+}
+
+template <class S, bool SR>
+static cudaError_t launch_batch_staged_t(const StepArgs &base, const BatchInst *inst,
+                                         const int4 *tiles, int ntiles, int parity,
+                                         const unsigned long long *tctr, int k, unsigned *err,
+                                         int nsm, cudaStream_t s) {
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      batch_staged_kernel<S, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      StageLayout<S>::kSmemBytes);
+  if (attr != cudaSuccess) return attr;
+  if (ntiles <= 0) return cudaSuccess;
+  const int grid = ntiles < nsm ? ntiles : nsm;
+  batch_staged_kernel<S, SR><<<grid, kStagedThreads, StageLayout<S>::kSmemBytes, s>>>(
+      base, inst, tiles, ntiles, parity, tctr, k, err);
+  return cudaGetLastError();
+}
+
+// Tile width of the staged kernel for a storage kind.
+inline int staged_tile_width(int storage) {
+  return storage == LBMP_STORE_FP32 ? StageCfg<StoreF32>::W : StageCfg<StoreF16>::W;
+}
+
 // Per-instance reductions: block partials over the work list (one 256-node
 // segment per item), then one block per instance sums its items in order.
 constexpr int kBatchMacroBX = 256;
@@ -188,8 +337,9 @@ __global__ void __launch_bounds__(256)
 struct Shape {
   int bx, npt, persistent;
 };
+// persistent = 2: the staged batched kernel (bx, npt unused)
 constexpr Shape kShapes[] = {{128, 1, 0}, {128, 2, 0}, {256, 1, 0}, {256, 2, 0}, {64, 4, 0},
-                             {128, 4, 0}, {128, 2, 1}, {256, 2, 1}, {64, 4, 1}};
+                             {128, 4, 0}, {128, 2, 1}, {256, 2, 1}, {64, 4, 1}, {0, 0, 2}};
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 
 template <class S, bool SR, int BX, int NPT>
@@ -231,7 +381,14 @@ static cudaError_t launch_shape_s(int shape, const BatchInst *inst, const long l
 static cudaError_t launch_batch_step(int storage, bool sr, int shape, const BatchInst *inst,
                                      const long long *cum, const int *item_inst, int parity,
                                      const unsigned long long *tctr, int k, int nsm,
-                                     long long items, cudaStream_t s) {
+                                     long long items, const StepArgs &base, const int4 *tiles,
+                                     int ntiles, unsigned *err, cudaStream_t s) {
+  if (kShapes[shape].persistent == 2) {
+    if (storage == LBMP_STORE_FP32)
+      return launch_batch_staged_t<StoreF32, false>(base, inst, tiles, ntiles, parity, tctr, k, err, nsm, s);
+    if (sr) return launch_batch_staged_t<StoreF16, true>(base, inst, tiles, ntiles, parity, tctr, k, err, nsm, s);
+    return launch_batch_staged_t<StoreF16, false>(base, inst, tiles, ntiles, parity, tctr, k, err, nsm, s);
+  }
   if (storage == LBMP_STORE_FP32)
     return launch_shape_s<StoreF32, false>(shape, inst, cum, item_inst, parity, tctr, k, nsm, items, s);
   if (sr)
@@ -293,6 +450,9 @@ struct lbmp_batch {
   double *d_med_partials = nullptr;  // set_fields scratch
   double *d_med_results = nullptr;
   unsigned *d_flag = nullptr;
+  unsigned *d_err = nullptr;         // raised by a bounded wait of the staged kernel
+  int4 *d_tiles = nullptr;           // tile list of the staged kernel
+  int ntiles = 0;
   unsigned long long *d_tctr = nullptr;
   int shape = 1;                     // index into kShapes (default 128 x 2)
   int parity = 0;
@@ -353,6 +513,11 @@ lbmp_status upload_cum(lbmp_batch *b, long long *d_cum, const std::vector<long l
 
 lbmp_status set_shape(lbmp_batch *b, int shape) {
   const lbmp::Shape sh = lbmp::kShapes[shape];
+  if (sh.persistent == 2) {  // staged: the tile list is built at creation
+    b->shape = shape;
+    bfree_graphs(b);
+    return LBMP_OK;
+  }
   std::vector<long long> cum = work_list(b, sh.bx * sh.npt);
   if (cum.back() > b->items_cap) return bfail(LBMP_ECUDA, "work-item table too small");
   std::vector<int> item_inst((size_t)cum.back());
@@ -372,7 +537,7 @@ lbmp_status launch_steps(lbmp_batch *b, int64_t n, cudaStream_t s, bool count_la
   for (int64_t t = 0; t < n; ++t) {
     BCK(lbmp::launch_batch_step(b->p.storage, b->sr, b->shape, b->d_inst, b->d_cum_step,
                                 b->d_item_inst, b->parity, b->d_tctr, (int)t, b->nsm,
-                                b->items_step, s));
+                                b->items_step, b->h_inst[0].a, b->d_tiles, b->ntiles, b->d_err, s));
     b->parity ^= 1;
     if (count_launches) b->launches++;
   }
@@ -543,7 +708,8 @@ lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32
     BTRY(balloc(b, (void **)&b->d_cum_macro, sizeof(long long) * (count + 1), "work list"));
     {
       int min_chunk = 1 << 30;
-      for (const auto &sh : lbmp::kShapes) min_chunk = std::min(min_chunk, sh.bx * sh.npt);
+      for (const auto &sh : lbmp::kShapes)
+        if (sh.persistent != 2) min_chunk = std::min(min_chunk, sh.bx * sh.npt);
       b->items_cap = work_list(b, min_chunk).back();
       BTRY(balloc(b, (void **)&b->d_item_inst, sizeof(int) * (size_t)b->items_cap, "work-item table"));
     }
@@ -555,6 +721,28 @@ lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32
     BTRY(balloc(b, (void **)&b->d_med_partials, sizeof(double) * lbmp::kNQ * max_mb, "medium partials"));
     BTRY(balloc(b, (void **)&b->d_med_results, sizeof(double) * lbmp::kNQ, "medium results"));
     BTRY(balloc(b, (void **)&b->d_flag, sizeof(unsigned), "validation flag"));
+    BTRY(balloc(b, (void **)&b->d_err, sizeof(unsigned), "wait error flag"));
+    e = cudaMemset(b->d_err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) BTRY(bcuda(e, "cudaMemset"));
+    {
+      // tile list of the staged kernel: W consecutive nodes of each
+      // instance's padded lattice over its fluid rows
+      const int W = lbmp::staged_tile_width(p.storage);
+      std::vector<int4> tiles;
+      for (int i = 0; i < count; ++i) {
+        const lbmp::StepArgs &a = b->h_inst[i].a;
+        const long long F0 = (long long)a.y0 * a.pitch;
+        const long long Fend = (long long)(a.y0 + b->h_inst[i].rows) * a.pitch;
+        for (long long T0 = F0; T0 < Fend; T0 += W)
+          tiles.push_back(make_int4(i, (int)(T0 % a.pitch), (int)(T0 / a.pitch),
+                                    a.y0 + b->h_inst[i].rows));
+      }
+      if (tiles.size() > 0x7fffffffu) BTRY(bfail(LBMP_EINVAL, "batch too large for the tile list"));
+      b->ntiles = (int)tiles.size();
+      BTRY(balloc(b, (void **)&b->d_tiles, tiles.size() * sizeof(int4), "tile list"));
+      e = cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) BTRY(bcuda(e, "tile list upload"));
+    }
     BTRY(balloc(b, (void **)&b->d_tctr, sizeof(unsigned long long), "time-level counter"));
     e = cudaMemset(b->d_tctr, 0, sizeof(unsigned long long));
     if (e != cudaSuccess) BTRY(bcuda(e, "cudaMemset"));
@@ -671,7 +859,22 @@ lbmp_status lbmp_batch_synchronize(lbmp_batch *b) {
   if (!b) return bfail(LBMP_EINVAL, "NULL batch");
   BCK(cudaSetDevice(b->device));
   BCK(cudaStreamSynchronize(b->stream));
+  unsigned err = 0;
+  BCK(cudaMemcpy(&err, b->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err) return bfail(LBMP_ETIMEOUT, "a bounded wait of the staged batched kernel gave up");
   return LBMP_OK;
+}
+
+lbmp_status lbmp_batch_set_shape(lbmp_batch *b, int32_t shape) {
+  try {
+    if (!b) return bfail(LBMP_EINVAL, "NULL batch");
+    if (shape < 0 || shape >= lbmp::kNumShapes)
+      return bfail(LBMP_EINVAL, "shape must be in [0, %d)", lbmp::kNumShapes);
+    BCK(cudaSetDevice(b->device));
+    return set_shape(b, shape);
+  } catch (...) {
+    return bfail(LBMP_ECUDA, "lbmp_batch_set_shape: unexpected exception");
+  }
 }
 
 lbmp_status lbmp_batch_permeability(lbmp_batch *b, double *k_g, double *u_mean) {
@@ -824,9 +1027,16 @@ lbmp_status lbmp_batch_tune(lbmp_batch *b, int32_t steps, int32_t *chosen, doubl
 lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out) {
   if (!b || !out) return bfail(LBMP_EINVAL, "NULL argument");
   out->count = b->count;
-  out->shape_threads = lbmp::kShapes[b->shape].bx;
-  out->shape_nodes_per_thread = lbmp::kShapes[b->shape].npt;
-  out->persistent = lbmp::kShapes[b->shape].persistent;
+  const lbmp::Shape sh = lbmp::kShapes[b->shape];
+  if (sh.persistent == 2) {  // staged: consumer threads and nodes per thread per tile
+    const int W = lbmp::staged_tile_width(b->p.storage);
+    out->shape_threads = lbmp::kConsumerWarps * 32;
+    out->shape_nodes_per_thread = W / (lbmp::kConsumerWarps * 32);
+  } else {
+    out->shape_threads = sh.bx;
+    out->shape_nodes_per_thread = sh.npt;
+  }
+  out->persistent = sh.persistent;
   out->total_nodes = b->total_nodes;
   out->steps = b->steps;
   out->launches = b->launches;

@@ -56,7 +56,7 @@ struct StageLayout {
   static constexpr int kStageBytes = kPopBytes + kMedBytes;
   static constexpr int kBarBytes = 128;  // full[STAGES], empty[STAGES]
   static constexpr int kSmemBytes = kBarBytes + C::STAGES * kStageBytes;
-  static_assert(kPopBytes % 16 == 0 && kStageBytes % 16 == 0, "16-byte stage alignment");
+  static_assert(kPopBytes % 16 == 0 && kMedBytes % 16 == 0, "16-byte stage alignment");
   static_assert(RW * (int)sizeof(T) % 16 == 0, "16-byte row alignment");
   static_assert(C::A * (int)sizeof(T) == 16, "halo of 16 bytes");
   static_assert(2 * C::STAGES * 8 <= kBarBytes, "barrier area");
@@ -239,6 +239,38 @@ __device__ __noinline__ void staged_edge_pair(const typename S::T *__restrict__ 
     S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? pair_bits(h, i) : 0u, 0u);
 }
 
+// Update of an interior node pair (2 <= x, x + 2 < nx, no plate
+// neighbour) at tile position c: every source is in the stage.
+template <class S, bool SR>
+__device__ __forceinline__ void staged_interior_pair(const typename S::T *__restrict__ sp,
+                                                     typename S::T *__restrict__ fout,
+                                                     const StepArgs &a, int c, int x, int y,
+                                                     float4 m, uint32_t ts) {
+  using L = StageLayout<S>;
+  constexpr int PL = L::RW;  // elements between planes in a stage
+  float dA[9], dB[9];
+  // e_x = 0 directions as one vector read per plane
+  const typename S::T *row = sp + StageCfg<S>::A + c;
+  S::ld2(row, dA[0], dB[0]);
+  S::ld2(row + 2 * PL, dA[2], dB[2]);
+  S::ld2(row + 4 * PL, dA[4], dB[4]);
+  dA[1] = S::ld1(row + 1 * PL - 1); dB[1] = S::ld1(row + 1 * PL);
+  dA[5] = S::ld1(row + 5 * PL - 1); dB[5] = S::ld1(row + 5 * PL);
+  dA[8] = S::ld1(row + 8 * PL - 1); dB[8] = S::ld1(row + 8 * PL);
+  dA[3] = S::ld1(row + 3 * PL + 1); dB[3] = S::ld1(row + 3 * PL + 2);
+  dA[6] = S::ld1(row + 6 * PL + 1); dB[6] = S::ld1(row + 6 * PL + 2);
+  dA[7] = S::ld1(row + 7 * PL + 1); dB[7] = S::ld1(row + 7 * PL + 2);
+  const NodeState nA = node_state(dA, m.x, m.y, a);
+  collide<S::kHiLo>(dA, nA, a);
+  const NodeState nB = node_state(dB, m.z, m.w, a);
+  collide<S::kHiLo>(dB, nB, a);
+  const long long o = (long long)y * a.pitch + x;
+  const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)  // 32 random bits per direction and pair
+    S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? pair_bits(h, i) : 0u, 0u);
+}
+
 // ------------------------------------------------------------------ kernel
 template <class S, bool SR>
 __global__ void __launch_bounds__(kStagedThreads, 1)
@@ -359,28 +391,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
         staged_edge_pair<S, SR>(sp, fin, fout, med, a, c, x, y, m, ts);
         continue;
       }
-      // interior pair: e_x = 0 directions as one vector read per plane
-      float dA[9], dB[9];
-      const T *row = sp + A + c;
-      constexpr int PL = RW;  // elements between planes in a stage
-      S::ld2(row, dA[0], dB[0]);
-      S::ld2(row + 2 * PL, dA[2], dB[2]);
-      S::ld2(row + 4 * PL, dA[4], dB[4]);
-      dA[1] = S::ld1(row + 1 * PL - 1); dB[1] = S::ld1(row + 1 * PL);
-      dA[5] = S::ld1(row + 5 * PL - 1); dB[5] = S::ld1(row + 5 * PL);
-      dA[8] = S::ld1(row + 8 * PL - 1); dB[8] = S::ld1(row + 8 * PL);
-      dA[3] = S::ld1(row + 3 * PL + 1); dB[3] = S::ld1(row + 3 * PL + 2);
-      dA[6] = S::ld1(row + 6 * PL + 1); dB[6] = S::ld1(row + 6 * PL + 2);
-      dA[7] = S::ld1(row + 7 * PL + 1); dB[7] = S::ld1(row + 7 * PL + 2);
-      const NodeState nA = node_state(dA, m.x, m.y, a);
-      collide<S::kHiLo>(dA, nA, a);
-      const NodeState nB = node_state(dB, m.z, m.w, a);
-      collide<S::kHiLo>(dB, nB, a);
-      const long long o = (long long)y * a.pitch + x;
-      const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
-#pragma unroll
-      for (int i = 0; i < 9; ++i)  // 32 random bits per direction and pair
-        S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? pair_bits(h, i) : 0u, 0u);
+      staged_interior_pair<S, SR>(sp, fout, a, c, x, y, m, ts);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty(s));

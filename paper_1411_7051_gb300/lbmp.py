@@ -166,6 +166,8 @@ def load(path: str = LIB_PATH):
     L.lbmp_batch_populations.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
     L.lbmp_batch_tune.restype = st
     L.lbmp_batch_tune.argtypes = [_VP, ctypes.c_int32, I32P, _D]
+    L.lbmp_batch_set_shape.restype = st
+    L.lbmp_batch_set_shape.argtypes = [_VP, ctypes.c_int32]
     L.lbmp_batch_get_info.restype = st
     L.lbmp_batch_get_info.argtypes = [_VP, ctypes.POINTER(BatchInfo)]
     _lib = L
@@ -559,6 +561,10 @@ class Batch:
         ms = ctypes.c_double()
         _check(load().lbmp_batch_tune(self._h, int(steps), ctypes.byref(chosen), ctypes.byref(ms)))
         return chosen.value, ms.value
+
+    def set_shape(self, shape: int):
+        """``lbmp_batch_set_shape``: use launch candidate ``shape``."""
+        _check(load().lbmp_batch_set_shape(self._h, int(shape)))
 
     def info(self) -> BatchInfo:
         out = BatchInfo()

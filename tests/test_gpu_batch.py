@@ -36,12 +36,17 @@ def _single(cfg, nx, ny, med):
     return s
 
 
+NSHAPES = 10   # launch candidates; the last is the staged bulk-copy kernel
+
+
+@pytest.mark.parametrize("shape", list(range(NSHAPES)))
 @pytest.mark.parametrize("storage,rounding", [(lbmp.STORE_FP32, lbmp.ROUND_STOCHASTIC),
                                               (lbmp.STORE_FP16, lbmp.ROUND_NEAREST)])
-def test_batch_instances_match_single_runs(storage, rounding):
+def test_batch_instances_match_single_runs(storage, rounding, shape):
     cfg = _cfg(storage, rounding)
     meds = _media()
     with lbmp.Batch(cfg, SIZES) as b:
+        b.set_shape(shape)
         for j, m in enumerate(meds):
             b.set_fields(j, m.eps, m.k_i, m.kn)
         b.step(70)   # two graph replays and six single launches
@@ -87,15 +92,34 @@ def test_batch_tuner_keeps_the_state():
     a.step(10)
     b.step(10)
     chosen, ms = a.tune(steps=4)
-    assert 0 <= chosen < 9 and ms > 0
+    assert 0 <= chosen < NSHAPES and ms > 0
     info = a.info()
-    assert info.shape_threads * info.shape_nodes_per_thread in (128, 256, 512)
+    assert info.shape_threads * info.shape_nodes_per_thread in (128, 256, 512, 1024, 2048)
     a.step(40)
     b.step(40)
     for j in range(len(SIZES)):
         np.testing.assert_allclose(a.populations(j).cpu().numpy(), b.populations(j).cpu().numpy(),
                                    rtol=0, atol=1e-12)
     assert a.info().steps == 50
+
+
+def test_batch_staged_fp16_sr_is_seeded_per_instance():
+    """The staged batched kernel mixes the instance index into the rounding
+    stream: two identical instances round differently, and a repeat of the
+    run reproduces both exactly."""
+    cfg = _cfg(lbmp.STORE_FP16, lbmp.ROUND_STOCHASTIC)
+    m = _media()[0]
+    runs = []
+    for _ in range(2):
+        with lbmp.Batch(cfg, [SIZES[0], SIZES[0]]) as b:
+            b.set_shape(NSHAPES - 1)
+            for j in range(2):
+                b.set_fields(j, m.eps, m.k_i, m.kn)
+            b.step(40)
+            b.synchronize()
+            runs.append([b.populations(j).cpu().numpy() for j in range(2)])
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert not np.array_equal(runs[0][0], runs[0][1])
 
 
 def test_batch_state_errors():
@@ -106,6 +130,9 @@ def test_batch_state_errors():
         with pytest.raises(lbmp.LbmpError) as ei:
             b.step(1)
         assert ei.value.status == lbmp.ESTATE
+        with pytest.raises(lbmp.LbmpError) as ei:
+            b.set_shape(NSHAPES)
+        assert ei.value.status == lbmp.EINVAL
     with pytest.raises(lbmp.LbmpError) as ei:
         lbmp.Batch(cfg, [(64, 40), (2, 10)])   # pressure columns need nx >= 3
     assert ei.value.status == lbmp.EINVAL
