@@ -47,7 +47,7 @@ def test_two_ranks_take_the_slowest_time():
     expected = 2 * 4096 * 4096 * 100 / (17.25e-3) / 1e9
     for rank, ms, value in out:
         assert ms == 17.25
-        assert value == pytest.approx(expected, rel=1e-12)
+        assert value == pytest.approx(expected, rel=1e-12, abs=0)
 
 
 def test_reference_arm_runs_on_rank_zero_only(capsys):

@@ -68,7 +68,7 @@ def test_gradient_every_node(orc, name):
     m = case.medium
     o.set_fields(m.eps, m.k_i, m.kn)
     o.step(N)
-    assert kg == pytest.approx(o.permeability()[0], rel=1e-5)
+    assert kg == pytest.approx(o.permeability()[0], rel=1e-5, abs=0)
     nodes = np.arange(case.nx * case.ny)
     fl = _fd(orc, case, N, nodes, "logk").reshape(case.ny, case.nx)
     fe = _fd(orc, case, N, nodes, "eps").reshape(case.ny, case.nx)
@@ -88,7 +88,7 @@ def test_staged_forward_kernel(orc):
     case = SMALL["pressure_walls_forch"]
     kg_d, gl_d, ge_d = _gpu_grad(case, 40, every=0, kernel=lbmp.KERNEL_DIRECT)
     kg_s, gl_s, ge_s = _gpu_grad(case, 40, every=0, kernel=lbmp.KERNEL_STAGED)
-    assert kg_s == pytest.approx(kg_d, rel=1e-6)
+    assert kg_s == pytest.approx(kg_d, rel=1e-6, abs=0)
     assert _rel(gl_s, gl_d) <= 1e-5 and _rel(ge_s, ge_d) <= 1e-5
 
 
@@ -128,11 +128,11 @@ def test_uniform_sum_rule(forch):
     med = media.Medium(np.full((ny, nx), eps0), np.full((ny, nx), k0), np.zeros((ny, nx)), "uniform")
     case = Case(nx, ny, tau=0.8, G=G, forchheimer=forch, medium=med)
     kg, gl, ge = _gpu_grad(case, N)
-    assert kg == pytest.approx(uniform_kg(np.log(k0), eps0, N, G, forch).real, rel=1e-5)
+    assert kg == pytest.approx(uniform_kg(np.log(k0), eps0, N, G, forch).real, rel=1e-5, abs=0)
     dk = complex_step(lambda z: uniform_kg(z, eps0, N, G, forch), np.log(k0))
     de = complex_step(lambda z: uniform_kg(np.log(k0), z, N, G, forch), eps0)
-    assert gl.sum() == pytest.approx(dk, rel=2e-5)
-    assert ge.sum() == pytest.approx(de, rel=2e-5)
+    assert gl.sum() == pytest.approx(dk, rel=2e-5, abs=0)
+    assert ge.sum() == pytest.approx(de, rel=2e-5, abs=0)
 
 
 def _adjoint_workload(n):
@@ -191,10 +191,10 @@ def test_full_size_workload():
             return s.permeability()[0]
 
     fd_k = (kg_of(med.eps, med.k_i * np.exp(h * d)) - kg_of(med.eps, med.k_i * np.exp(-h * d))) / (2 * h)
-    assert float((gl * d).sum()) == pytest.approx(fd_k, rel=2e-3)
+    assert float((gl * d).sum()) == pytest.approx(fd_k, rel=2e-3, abs=0)
     de = 0.1 * d * med.eps
     fd_e = (kg_of(med.eps + h * de, med.k_i) - kg_of(med.eps - h * de, med.k_i)) / (2 * h)
-    assert float((ge * de).sum()) == pytest.approx(fd_e, rel=2e-3)
+    assert float((ge * de).sum()) == pytest.approx(fd_e, rel=2e-3, abs=0)
     torch.cuda.empty_cache()
 
 
@@ -215,7 +215,7 @@ def test_autograd_function():
         # without a gradient request: the plain run
         with torch.no_grad():
             J2 = lbmp.ka_from_fields(s, log_k, eps, kn, N)
-    assert J.item() == pytest.approx(kg_ref, rel=1e-6)
+    assert J.item() == pytest.approx(kg_ref, rel=1e-6, abs=0)
     assert J2.item() == J.item()
     assert np.allclose(log_k.grad.cpu().numpy(), 3.0 * gl_ref.numpy(), rtol=1e-5, atol=1e-14)
     assert np.allclose(eps.grad.cpu().numpy(), 3.0 * ge_ref.numpy(), rtol=1e-5, atol=1e-14)

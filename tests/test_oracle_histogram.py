@@ -65,3 +65,21 @@ def test_trimodal_generator():
     assert np.all(m.eps[lab == media.PORE] == 1.0) and np.all(np.isinf(m.k_i[lab == media.PORE]))
     assert np.all(m.eps[lab == media.IMPERMEABLE] == 0.0)
     assert np.all(m.kn[lab == media.PERMEABLE] == 0.3)
+
+
+def test_layered_darcy_flow_bins():
+    """Periodic lattice of Darcy layers: row y has k proportional to y + 1/2
+    under a strong drag (eps nu / k >= 500 per step), so its steady velocity
+    is G k_y / nu to ~1e-4 (the viscous coupling of the layers) and
+    u0 = (y + 1/2) / (ny - 1/2).  With ny = 10 rows and 10 bins every row
+    falls in a bin of its own, at least 0.05 of a bin from its edges."""
+    nx, ny, nb = 4, 10, 10
+    k_row = 1e-4 * (np.arange(ny) + 0.5) / ny
+    p = orc.make_params(nx, ny, tau=0.8, G=(1e-5, 0.0))
+    s = orc.OracleSim(p)
+    s.set_fields(0.5, np.repeat(k_row[:, None], nx, axis=1), 0.0)
+    s.run_to_steady(tol=1e-12, check_every=200)
+    counts, umax = s.velocity_histogram(nb)
+    assert list(counts) == [nx] * nb
+    nu = (0.8 - 0.5) / 3.0
+    assert umax == pytest.approx(1e-5 * k_row[-1] / nu, rel=1e-3, abs=0)

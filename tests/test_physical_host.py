@@ -17,16 +17,16 @@ def L():
 def test_formulas_match_oracle(L, orc):
     for eps in (0.02, 0.3, 0.75):
         for d in (40e-9, 2e-6):
-            assert lbmp.kozeny_carman(eps, d) == pytest.approx(orc.kozeny_carman(eps, d), rel=1e-14)
+            assert lbmp.kozeny_carman(eps, d) == pytest.approx(orc.kozeny_carman(eps, d), rel=1e-14, abs=0)
     for k_d in (1e-22, 5e-17, 1e-12):
         for eps in (0.05, 0.5):
-            assert lbmp.pore_radius(k_d, eps) == pytest.approx(orc.pore_radius(k_d, eps), rel=1e-14)
+            assert lbmp.pore_radius(k_d, eps) == pytest.approx(orc.pore_radius(k_d, eps), rel=1e-14, abs=0)
     for mu, p in ((1.4e-5, 689475.0), (2.0e-5, 2.76e7)):
         assert lbmp.mean_free_path(mu, p, 323.0, 16e-3) == pytest.approx(
-            orc.mean_free_path(mu, p, 323.0, 16e-3), rel=1e-14)
+            orc.mean_free_path(mu, p, 323.0, 16e-3), rel=1e-14, abs=0)
     for kn in (0.0, 1e-4, 0.3, 5.0):
-        assert lbmp.fc_model(lbmp.KN_BKC, kn) == pytest.approx(orc.fc(kn), rel=1e-15)
-        assert lbmp.fc_model(lbmp.KN_FIRST_ORDER, kn) == pytest.approx(orc.fc_first_order(kn), rel=1e-15)
+        assert lbmp.fc_model(lbmp.KN_BKC, kn) == pytest.approx(orc.fc(kn), rel=1e-15, abs=0)
+        assert lbmp.fc_model(lbmp.KN_FIRST_ORDER, kn) == pytest.approx(orc.fc_first_order(kn), rel=1e-15, abs=0)
     assert math.isnan(lbmp.fc_model(7, 0.1))
     assert math.isnan(lbmp.kozeny_carman(1.0, 1e-6))
     assert math.isnan(lbmp.mean_free_path(0.0, 1e5, 300.0, 0.016))
@@ -46,8 +46,8 @@ def test_physical_medium(L, orc):
     for (y, x), e in np.ndenumerate(eps):
         if 0.0 < e < 1.0:
             kd = orc.kozeny_carman(e, d[y, x])
-            assert k_i[y, x] == pytest.approx(kd / dx ** 2, rel=1e-14)
-            assert kn[y, x] == pytest.approx(lam / orc.pore_radius(kd, e), rel=1e-14)
+            assert k_i[y, x] == pytest.approx(kd / dx ** 2, rel=1e-14, abs=0)
+            assert kn[y, x] == pytest.approx(lam / orc.pore_radius(kd, e), rel=1e-14, abs=0)
     # scalar grain diameter
     k2, kn2 = lbmp.physical_medium(eps, 40e-9, lam, dx)
     assert k2.shape == eps.shape
