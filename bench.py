@@ -621,7 +621,8 @@ def run_batch(args, ws, rank, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"of {kind}",
                          "bytes_per_update": info.bytes_per_update, "traffic": None,
-                         "kernel": "lbmp::batch_step_kernel"},
+                         "kernel": ("lbmp::batch_staged_kernel" if int(info.persistent) == 2
+                                    else "lbmp::batch_step_kernel")},
             "gpu_launches": int(info.launches - l0), "clocks": clk.summary(),
             "setup_s": setup_s, "tuned_shape_index": chosen, "tune_ms_per_step": tune_ms,
             "k_g_range": [float(np.min(kg)), float(np.max(kg))],

@@ -121,6 +121,28 @@ __global__ void __launch_bounds__(BX)
 // x and y of its first node, end of the instance's fluid rows).  The physics
 // shared by all instances comes in `base`; per tile the consumers override
 // the instance's geometry and FP16 scale, which then live in registers.
+// The producer, which runs stages ahead, looks the tile and its instance up
+// and leaves them in a per-stage header next to the copies (published by the
+// same mbarrier phase), so the consumers never wait on a global load at a
+// tile start.
+struct TileHead {
+  const void *fin;      // population buffer read this step
+  void *fout;           // population buffer written this step
+  const float2 *med;    // medium of the instance
+  long long plane;      // elements per plane
+  int nx, ny, pitch;    // geometry of the instance
+  int x, y, y_end;      // first node of the tile, end of the fluid rows
+  float scale, inv_scale;  // FP16 scale of the instance
+  uint32_t mix;         // stochastic-rounding stream of the instance
+  int pad[3];
+};
+constexpr int kHeadBytes = 128;
+static_assert(sizeof(TileHead) <= kHeadBytes && sizeof(TileHead) % 16 == 0, "tile header");
+template <class S>
+constexpr int batch_smem_bytes() {
+  return StageLayout<S>::kSmemBytes + StageCfg<S>::STAGES * kHeadBytes;
+}
+
 template <class S, bool SR>
 __global__ void __launch_bounds__(kStagedThreads, 1)
     batch_staged_kernel(const StepArgs base, const BatchInst *__restrict__ inst,
@@ -168,7 +190,25 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
       const long long T0 = (long long)tr.z * pitch + tr.y;
       const long long Fend = (long long)tr.w * pitch;
       const uint32_t med_bytes = (uint32_t)(min((long long)W, Fend - T0) * 8);
-      if (lane == 0) mbar_arrive_expect_tx(full(s), 9u * kPlaneBytes + med_bytes);
+      if (lane == 0) {
+        // the header is a plain store ordered before the arrival (release);
+        // the consumers' wait on the phase acquires it
+        TileHead *h = reinterpret_cast<TileHead *>(smem + L::kSmemBytes + s * kHeadBytes);
+        h->fin = I.buf[parity];
+        h->fout = I.buf[parity ^ 1];
+        h->med = I.med;
+        h->plane = I.a.plane;
+        h->nx = I.a.nx;
+        h->ny = I.a.ny;
+        h->pitch = pitch;
+        h->x = tr.y;
+        h->y = tr.z;
+        h->y_end = tr.w;
+        h->scale = I.a.scale;
+        h->inv_scale = I.a.inv_scale;
+        h->mix = mix32((uint32_t)I.index * 0x85ebca77u + 1u);
+        mbar_arrive_expect_tx(full(s), 9u * kPlaneBytes + med_bytes);
+      }
       __syncwarp();
       const uint32_t st = sbase + (uint32_t)L::kBarBytes + (uint32_t)s * (uint32_t)L::kStageBytes;
       if (lane < 9) {
@@ -204,38 +244,40 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
     const int s = it % NS;
     if (!mbar_wait(full(s), (uint32_t)(it / NS) & 1u, err)) return;
-    const int4 tr = tiles[t];
-    const BatchInst &I = inst[tr.x];
-    const T *fin = (const T *)I.buf[parity];
-    T *fout = (T *)I.buf[parity ^ 1];
-    const float2 *med = I.med;
+    const TileHead h = *reinterpret_cast<const TileHead *>(smem + L::kSmemBytes + s * kHeadBytes);
+    const T *fin = (const T *)h.fin;
+    T *fout = (T *)h.fout;
+    const float2 *med = h.med;
     const unsigned char *sb = smem + L::kBarBytes + s * L::kStageBytes;
     const T *sp = reinterpret_cast<const T *>(sb);
     const float2 *sm = reinterpret_cast<const float2 *>(sb + L::kPopBytes);
     StepArgs a = base;
-    a.nx = I.a.nx;
-    a.ny = I.a.ny;
-    a.pitch = I.a.pitch;
-    a.plane = I.a.plane;
-    a.scale = I.a.scale;
-    a.inv_scale = I.a.inv_scale;
-    const uint32_t tsi = SR ? ts ^ mix32((uint32_t)I.index * 0x85ebca77u + 1u) : 0u;
+    a.nx = h.nx;
+    a.ny = h.ny;
+    a.pitch = h.pitch;
+    a.plane = h.plane;
+    a.scale = h.scale;
+    a.inv_scale = h.inv_scale;
+    const uint32_t tsi = SR ? ts ^ h.mix : 0u;
 #pragma unroll 1
     for (int j = 0; j < kPairs; ++j) {
       const int c = 2 * (threadIdx.x + j * kConsumerWarps * 32);
-      int x = tr.y + c, y = tr.z;
+      int x = h.x + c, y = h.y;
       while (x >= a.pitch) {
         x -= a.pitch;
         ++y;
       }
-      if (y >= tr.w || x >= a.nx) continue;
+      if (y >= h.y_end || x >= a.nx) continue;
+      if (x == 0 || x + 2 >= a.nx) continue;  // column edges: the pass below
       const float4 m = *reinterpret_cast<const float4 *>(sm + c);
-      if (x == 0 || x + 2 >= a.nx || (a.walls && (y == 1 || y == a.ny - 2))) {
+      if (a.walls && (y == 1 || y == a.ny - 2)) {
         staged_edge_pair<S, SR>(sp, fin, fout, med, a, c, x, y, m, tsi);
         continue;
       }
       staged_interior_pair<S, SR>(sp, fout, a, c, x, y, m, tsi);
     }
+    staged_column_edges<S, SR>(sp, fin, fout, med, a, sm, h.x, h.y, h.y_end, tsi,
+                               it % kConsumerWarps);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty(s));
   }
@@ -248,11 +290,11 @@ static cudaError_t launch_batch_staged_t(const StepArgs &base, const BatchInst *
                                          int nsm, cudaStream_t s) {
   static const cudaError_t attr = cudaFuncSetAttribute(
       batch_staged_kernel<S, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      StageLayout<S>::kSmemBytes);
+      batch_smem_bytes<S>());
   if (attr != cudaSuccess) return attr;
   if (ntiles <= 0) return cudaSuccess;
   const int grid = ntiles < nsm ? ntiles : nsm;
-  batch_staged_kernel<S, SR><<<grid, kStagedThreads, StageLayout<S>::kSmemBytes, s>>>(
+  batch_staged_kernel<S, SR><<<grid, kStagedThreads, batch_smem_bytes<S>(), s>>>(
       base, inst, tiles, ntiles, parity, tctr, k, err);
   return cudaGetLastError();
 }

@@ -181,77 +181,177 @@ __device__ __forceinline__ void pull_node(const typename S::T *__restrict__ fin,
   d[8] = wp ? S::ld1(fin + 6 * P + r + x) : S::ld1(fin + 8 * P + rp + xm);
 }
 
-// ---------------------------------------------------- macroscopic state
-struct NodeState {
-  float drho_s;  // (rho - rho0) * S
-  float mx, my;  // momentum sum_i f_i e_i, stored units
-  float rho;     // physical density
-  float ux, uy;  // physical velocity (Eq. 17 / quadratic form)
-  float Fx, Fy;  // total force (Eq. 2 / Eq. 8)
-  float rFx, rFy;  // rho S F (stored units): the momentum the force adds
-  float ieps;    // 1 / eps (0 for an impermeable node)
-};
+// ------------------------------------------------- explicit FP32 arithmetic
+// The node update is written once over a lane type V: float for one node,
+// float2 for a node pair held in the two lanes and computed with the packed
+// FP32 instructions of sm_100 and later (add / mul / fma .f32x2), whose
+// lanes round exactly as the scalar operations do.  Every operation is
+// spelled out (no multiply-add contraction left to the compiler), so a node
+// gives the same bits on either path, and the pair path issues about half
+// the arithmetic instructions.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float vrcp(float a) { return rcp_approx(a); }
+__device__ __forceinline__ float vsqrt(float a) { return sqrt_approx(a); }
 
-// Eq. 16a, Eq. 16b solved for u (Eq. 17, or u = v / (c0 + sqrt(c0^2 +
-// c1|v|)) with the Forchheimer term), and F of Eq. 2.  eps = 0 is an
-// impermeable node: u = 0 and F = -2 m / rho (Eq. 16b with u = 0).
-// DYN: inv_k is 1/k_i and kn0 the node's Kn at p0; its apparent
-// permeability k_a = k_i f_c(kn0 p0 / p) (Eq. 3) follows the pressure
-// p / p0 = 1 + kn_beta (rho - rho0) of the node.
+// The packed forms are inline PTX with an explicit .rn.  The code generator
+// may still fuse a packed multiply into a packed add that consumes it
+// (observed: ~10% of the updates then differ in the last bit from the
+// one-node path, and the difference moves with the surrounding code), so
+// the update below never adds or subtracts the result of a multiply: each
+// such pair is written as one fma on both paths.
+#define LBMP_F32X2_2(op)                                                      \
+  float2 r;                                                                   \
+  asm("{\n\t.reg .b64 p, q, t;\n\t"                                       \
+      "mov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t" op               \
+      " t, p, q;\n\tmov.b64 {%0, %1}, t;\n\t}"                            \
+      : "=f"(r.x), "=f"(r.y)                                                  \
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                              \
+  return r
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { LBMP_F32X2_2("add.rn.f32x2"); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { LBMP_F32X2_2("sub.rn.f32x2"); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { LBMP_F32X2_2("mul.rn.f32x2"); }
+#undef LBMP_F32X2_2
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n\t.reg .b64 p, q, s, t;\n\t"
+      "mov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\tmov.b64 s, {%6, %7};\n\t"
+      "fma.rn.f32x2 t, p, q, s;\n\tmov.b64 {%0, %1}, t;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 vrcp(float2 a) {
+  return make_float2(rcp_approx(a.x), rcp_approx(a.y));
+}
+__device__ __forceinline__ float2 vsqrt(float2 a) {
+  return make_float2(sqrt_approx(a.x), sqrt_approx(a.y));
+}
+
+template <class V>
+__device__ __forceinline__ V vsplat(float s);
+template <>
+__device__ __forceinline__ float vsplat<float>(float s) { return s; }
+template <>
+__device__ __forceinline__ float2 vsplat<float2>(float s) { return make_float2(s, s); }
+
+// ---------------------------------------------------- macroscopic state
+template <class V>
+struct NodeStateT {
+  V drho_s;  // (rho - rho0) * S
+  V mx, my;  // momentum sum_i f_i e_i, stored units
+  V rho;     // physical density
+  V ux, uy;  // physical velocity (Eq. 17 / quadratic form)
+  V Fx, Fy;  // total force (Eq. 2 / Eq. 8)
+  V rFx, rFy;  // rho S F (stored units): the momentum the force adds
+  V ieps;    // 1 / eps (0 for an impermeable node)
+};
+using NodeState = NodeStateT<float>;
+
+// Velocity and force of a permeable node (eps > 0): v = m / rho + eps G / 2,
+// u = v / (c0 + sqrt(c0^2 + c1 |v|)) (Eq. 17 when c1 = 0, i.e. without the
+// Forchheimer term), F = eps G - (eps nu / k_a + eps F_eps |u| / sqrt(k_a)) u
+// (Eq. 2).  c = 1 / (S rho).
+template <class V>
+__device__ __forceinline__ void porous_state(NodeStateT<V> &s, V eps, V inv_k, V c,
+                                             const StepArgs &a) {
+  s.ieps = vrcp(eps);
+  const V eGx = vmul(eps, vsplat<V>(a.Gx)), eGy = vmul(eps, vsplat<V>(a.Gy));
+  const V vx = vfma(vsplat<V>(0.5f), eGx, vmul(s.mx, c));
+  const V vy = vfma(vsplat<V>(0.5f), eGy, vmul(s.my, c));
+  const V darcy = vmul(vmul(eps, vsplat<V>(a.nu)), inv_k);  // eps nu / k_a
+  const V c0 = vfma(vsplat<V>(0.25f), darcy, vsplat<V>(0.5f));  // (1 + eps nu / (2 k_a)) / 2
+  V idn, drag;
+  if (a.forch) {
+    // c1 = eps F_eps / (2 sqrt(k_a)) with F_eps = 1.75 / sqrt(150 eps^3)
+    const V c1 = vmul(vsplat<V>(a.fe_half), vsqrt(vmul(inv_k, s.ieps)));
+    const V vmag = vsqrt(vfma(vx, vx, vmul(vy, vy)));
+    idn = vrcp(vadd(c0, vsqrt(vfma(c0, c0, vmul(c1, vmag)))));
+    // eps nu / k_a + eps F_eps |u| / sqrt(k_a)
+    drag = vfma(vmul(vsplat<V>(2.0f), c1), vmul(vmag, idn), darcy);
+  } else {
+    idn = vrcp(vmul(vsplat<V>(2.0f), c0));
+    drag = darcy;
+  }
+  s.ux = vmul(vx, idn);
+  s.uy = vmul(vy, idn);
+  s.Fx = vfma(vneg(drag), s.ux, eGx);
+  s.Fy = vfma(vneg(drag), s.uy, eGy);
+  const V rs = vmul(s.rho, vsplat<V>(a.scale));
+  s.rFx = vmul(rs, s.Fx);
+  s.rFy = vmul(rs, s.Fy);
+}
+
+// An impermeable node (eps = 0): u = 0, F = -2 m / rho (Eq. 16b with u = 0).
+// rho F = -2 m exactly: the collision then reverses the momentum of the node
+// exactly (a rounded rho * (1 / rho) would make it grow or decay by ~1e-7
+// per step, compounding over the run).
+template <class V>
+__device__ __forceinline__ void solid_state(NodeStateT<V> &s, V c) {
+  s.ieps = vsplat<V>(0.0f);
+  s.ux = vsplat<V>(0.0f);
+  s.uy = vsplat<V>(0.0f);
+  s.rFx = vmul(vsplat<V>(-2.0f), s.mx);
+  s.rFy = vmul(vsplat<V>(-2.0f), s.my);
+  s.Fx = vmul(s.rFx, c);
+  s.Fy = vmul(s.rFy, c);
+}
+
+// Moments of Eq. 16a and the state of a node (one node, or a pair of nodes
+// in the lanes of V).  DYN (one node only): inv_k is 1/k_i and kn0 the
+// node's Kn at p0; its apparent permeability k_a = k_i f_c(kn0 p0 / p)
+// (Eq. 3) follows the pressure p / p0 = 1 + kn_beta (rho - rho0).
+template <class V, bool DYN = false>
+__device__ __forceinline__ NodeStateT<V> node_state_t(const V d[9], V eps, V inv_k,
+                                                      const StepArgs &a, float kn0 = 0.0f) {
+  NodeStateT<V> s;
+  s.drho_s = vadd(vadd(vadd(d[0], vadd(d[1], d[3])), vadd(d[2], d[4])),
+                  vadd(vadd(d[5], d[7]), vadd(d[6], d[8])));
+  // sum_i w_i e_i = 0, so the momentum of the deviations is the momentum.
+  const V d57 = vsub(d[5], d[7]);
+  s.mx = vadd(vsub(d[1], d[3]), vadd(d57, vsub(d[8], d[6])));
+  s.my = vadd(vsub(d[2], d[4]), vadd(d57, vsub(d[6], d[8])));
+  s.rho = vfma(s.drho_s, vsplat<V>(a.inv_scale), vsplat<V>(a.rho0));
+  const V c = vmul(vsplat<V>(a.inv_scale), vrcp(s.rho));  // 1 / (S rho)
+  if constexpr (sizeof(V) == sizeof(float)) {
+    if (eps > 0.0f) {
+      if (DYN) {
+        const float q = fmaf(a.kn_beta, s.drho_s * a.inv_scale, 1.0f);
+        inv_k = inv_k / fc_f32(kn0 / q, a.kn_model);
+      }
+      porous_state(s, eps, inv_k, c, a);
+    } else {
+      solid_state(s, c);
+    }
+  } else {
+    static_assert(!DYN, "the pair path has a static Kn");
+    // both forms, then each lane keeps its own
+    NodeStateT<V> q = s;
+    porous_state(s, eps, inv_k, c, a);
+    solid_state(q, c);
+    const bool px = eps.x > 0.0f, py = eps.y > 0.0f;
+#define LBMP_PICK(f) s.f = make_float2(px ? s.f.x : q.f.x, py ? s.f.y : q.f.y)
+    LBMP_PICK(ieps);
+    LBMP_PICK(ux);
+    LBMP_PICK(uy);
+    LBMP_PICK(Fx);
+    LBMP_PICK(Fy);
+    LBMP_PICK(rFx);
+    LBMP_PICK(rFy);
+#undef LBMP_PICK
+  }
+  return s;
+}
+
+// One node (the form every kernel but the staged pair path uses).
 template <bool DYN = false>
 __device__ __forceinline__ NodeState node_state(const float d[9], float eps, float inv_k,
                                                 const StepArgs &a, float kn0 = 0.0f) {
-  NodeState s;
-  s.drho_s = ((d[0] + (d[1] + d[3])) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
-  // sum_i w_i e_i = 0, so the momentum of the deviations is the momentum.
-  const float mx = (d[1] - d[3]) + ((d[5] - d[7]) + (d[8] - d[6]));
-  const float my = (d[2] - d[4]) + ((d[5] - d[7]) + (d[6] - d[8]));
-  s.mx = mx;
-  s.my = my;
-  s.rho = fmaf(s.drho_s, a.inv_scale, a.rho0);
-  const float c = a.inv_scale * rcp_approx(s.rho);  // 1 / (S rho)
-  if (eps > 0.0f) {
-    if (DYN) {
-      const float q = fmaf(a.kn_beta, s.drho_s * a.inv_scale, 1.0f);
-      inv_k = inv_k / fc_f32(kn0 / q, a.kn_model);
-    }
-    s.ieps = rcp_approx(eps);
-    const float eGx = eps * a.Gx, eGy = eps * a.Gy;
-    const float vx = fmaf(0.5f, eGx, mx * c);
-    const float vy = fmaf(0.5f, eGy, my * c);
-    const float darcy = eps * a.nu * inv_k;       // eps nu / k_a
-    const float c0 = fmaf(0.25f, darcy, 0.5f);    // (1 + eps nu / (2 k_a)) / 2
-    float idn, drag;
-    if (a.forch) {
-      // c1 = eps F_eps / (2 sqrt(k_a)) with F_eps = 1.75 / sqrt(150 eps^3)
-      const float c1 = a.fe_half * sqrt_approx(inv_k * s.ieps);
-      const float vmag = sqrt_approx(fmaf(vx, vx, vy * vy));
-      idn = rcp_approx(c0 + sqrt_approx(fmaf(c0, c0, c1 * vmag)));
-      drag = fmaf(2.0f * c1, vmag * idn, darcy);  // eps nu/k_a + eps F_eps |u| / sqrt(k_a)
-    } else {
-      idn = rcp_approx(2.0f * c0);
-      drag = darcy;
-    }
-    s.ux = vx * idn;
-    s.uy = vy * idn;
-    s.Fx = fmaf(-drag, s.ux, eGx);
-    s.Fy = fmaf(-drag, s.uy, eGy);
-    const float rs = s.rho * a.scale;
-    s.rFx = rs * s.Fx;
-    s.rFy = rs * s.Fy;
-  } else {
-    s.ieps = 0.0f;
-    s.ux = 0.0f;
-    s.uy = 0.0f;
-    s.Fx = -2.0f * mx * c;
-    s.Fy = -2.0f * my * c;
-    // rho F = -2 m exactly: the collision then reverses the momentum of an
-    // impermeable node exactly (a rounded rho * (1 / rho) would make it
-    // grow or decay by ~1e-7 per step, compounding over the run)
-    s.rFx = -2.0f * mx;
-    s.rFy = -2.0f * my;
-  }
-  return s;
+  return node_state_t<float, DYN>(d, eps, inv_k, a, kn0);
 }
 
 // Eq. 12 with the equilibrium of Eq. 14 and the forcing of Eq. 15 (last term
@@ -272,42 +372,49 @@ constexpr float kW0l = (float)(4.0 / 9.0 - (double)kW0h);
 constexpr float kW1l = (float)(1.0 / 9.0 - (double)kW1h);
 constexpr float kW2l = (float)(1.0 / 36.0 - (double)kW2h);
 
-template <bool HILO>
-__device__ __forceinline__ float wmul(float wh, float wl, float t) {
-  return HILO ? fmaf(wh, t, wl * t) : wh * t;
+template <bool HILO, class V>
+__device__ __forceinline__ V wmul(float wh, float wl, V t) {
+  if (HILO) return vfma(vsplat<V>(wh), t, vmul(vsplat<V>(wl), t));
+  return vmul(vsplat<V>(wh), t);
 }
 
 // HILO = false drops the lo parts of the weights: for FP16 storage the FP16
 // rounding (zero-mean with stochastic rounding) dominates their effect.
+template <bool HILO, class V>
+__device__ __forceinline__ void collide_t(V d[9], const NodeStateT<V> &s, const StepArgs &a) {
+  const V rs = vmul(s.rho, vsplat<V>(a.scale));
+  const V ux = s.ux, uy = s.uy, Fx = s.Fx, Fy = s.Fy, ie = s.ieps;
+  const V om = vsplat<V>(a.omega), cf = vsplat<V>(a.cforce);
+  const V usq = vmul(vmul(vsplat<V>(1.5f), ie), vfma(ux, ux, vmul(uy, uy)));
+  const V uF3 = vmul(vmul(vsplat<V>(3.0f), ie), vfma(ux, Fx, vmul(uy, Fy)));
+  const V A = vfma(om, s.drho_s, vneg(vmul(rs, vfma(om, usq, vmul(cf, uF3)))));
+  // P = 3 (X, Y); every sum with a product below is one fma
+  const V X = vfma(om, s.mx, s.rFx), Y = vfma(om, s.my, s.rFy);
+  const V three = vsplat<V>(3.0f), mthree = vsplat<V>(-3.0f);
+  const V qq = vmul(vmul(vsplat<V>(a.omega * 4.5f), ie), rs);
+  const V gg = vmul(vmul(vsplat<V>(a.cforce * 9.0f), ie), rs);
+  const V tx = vfma(qq, ux, vmul(gg, Fx)), ty = vfma(qq, uy, vmul(gg, Fy));  // M_xx / u_x, M_yy / u_y
+  const V Mxy2 = vfma(vmul(vmul(vsplat<V>(2.0f), qq), ux), uy,
+                      vmul(gg, vfma(ux, Fy, vmul(uy, Fx))));  // 2 M_xy
+  const V sx = vfma(ux, tx, A), sy = vfma(uy, ty, A), sd = vfma(uy, ty, sx);
+  const V s5 = vadd(sd, Mxy2), s6 = vsub(sd, Mxy2);
+  const V Py = vmul(three, Y);
+  const V pp = vfma(three, X, Py), pm = vfma(three, X, vneg(Py));
+  const V o1 = vsplat<V>(a.one_m_omega);
+  d[0] = vfma(o1, d[0], wmul<HILO>(kW0h, kW0l, A));
+  d[1] = vfma(o1, d[1], wmul<HILO>(kW1h, kW1l, vfma(three, X, sx)));
+  d[3] = vfma(o1, d[3], wmul<HILO>(kW1h, kW1l, vfma(mthree, X, sx)));
+  d[2] = vfma(o1, d[2], wmul<HILO>(kW1h, kW1l, vfma(three, Y, sy)));
+  d[4] = vfma(o1, d[4], wmul<HILO>(kW1h, kW1l, vfma(mthree, Y, sy)));
+  d[5] = vfma(o1, d[5], wmul<HILO>(kW2h, kW2l, vadd(s5, pp)));
+  d[7] = vfma(o1, d[7], wmul<HILO>(kW2h, kW2l, vsub(s5, pp)));
+  d[6] = vfma(o1, d[6], wmul<HILO>(kW2h, kW2l, vsub(s6, pm)));
+  d[8] = vfma(o1, d[8], wmul<HILO>(kW2h, kW2l, vadd(s6, pm)));
+}
+
 template <bool HILO = true>
 __device__ __forceinline__ void collide(float d[9], const NodeState &s, const StepArgs &a) {
-  const float mx = s.mx, my = s.my;
-  const float rs = s.rho * a.scale;
-  const float ux = s.ux, uy = s.uy, Fx = s.Fx, Fy = s.Fy, ie = s.ieps;
-  const float om = a.omega, cf = a.cforce;
-  const float usq = 1.5f * ie * fmaf(ux, ux, uy * uy);
-  const float uF3 = 3.0f * ie * fmaf(ux, Fx, uy * Fy);
-  const float A = fmaf(om, s.drho_s, -rs * fmaf(om, usq, cf * uF3));
-  const float Px = 3.0f * fmaf(om, mx, s.rFx);
-  const float Py = 3.0f * fmaf(om, my, s.rFy);
-  const float qq = om * 4.5f * ie * rs;
-  const float gg = cf * 9.0f * ie * rs;
-  const float Mxx = ux * fmaf(qq, ux, gg * Fx);
-  const float Myy = uy * fmaf(qq, uy, gg * Fy);
-  const float Mxy2 = fmaf(2.0f * qq * ux, uy, gg * fmaf(ux, Fy, uy * Fx));  // 2 M_xy
-  const float sx = A + Mxx, sy = A + Myy, sd = sx + Myy;
-  const float s5 = sd + Mxy2, s6 = sd - Mxy2;
-  const float pp = Px + Py, pm = Px - Py;
-  const float o1 = a.one_m_omega;
-  d[0] = fmaf(o1, d[0], wmul<HILO>(kW0h, kW0l, A));
-  d[1] = fmaf(o1, d[1], wmul<HILO>(kW1h, kW1l, sx + Px));
-  d[3] = fmaf(o1, d[3], wmul<HILO>(kW1h, kW1l, sx - Px));
-  d[2] = fmaf(o1, d[2], wmul<HILO>(kW1h, kW1l, sy + Py));
-  d[4] = fmaf(o1, d[4], wmul<HILO>(kW1h, kW1l, sy - Py));
-  d[5] = fmaf(o1, d[5], wmul<HILO>(kW2h, kW2l, s5 + pp));
-  d[7] = fmaf(o1, d[7], wmul<HILO>(kW2h, kW2l, s5 - pp));
-  d[6] = fmaf(o1, d[6], wmul<HILO>(kW2h, kW2l, s6 - pm));
-  d[8] = fmaf(o1, d[8], wmul<HILO>(kW2h, kW2l, s6 + pm));
+  collide_t<HILO, float>(d, s, a);
 }
 
 // Deviation of the porous equilibrium (Eq. 14) from w_i rho0, physical

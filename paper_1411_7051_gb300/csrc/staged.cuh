@@ -240,7 +240,9 @@ __device__ __noinline__ void staged_edge_pair(const typename S::T *__restrict__ 
 }
 
 // Update of an interior node pair (2 <= x, x + 2 < nx, no plate
-// neighbour) at tile position c: every source is in the stage.
+// neighbour) at tile position c: every source is in the stage.  The pair is
+// computed in the two lanes of float2 values (packed FP32 arithmetic); each
+// lane gives the bits of the one-node update.
 template <class S, bool SR>
 __device__ __forceinline__ void staged_interior_pair(const typename S::T *__restrict__ sp,
                                                      typename S::T *__restrict__ fout,
@@ -248,27 +250,57 @@ __device__ __forceinline__ void staged_interior_pair(const typename S::T *__rest
                                                      float4 m, uint32_t ts) {
   using L = StageLayout<S>;
   constexpr int PL = L::RW;  // elements between planes in a stage
-  float dA[9], dB[9];
-  // e_x = 0 directions as one vector read per plane
+  float2 d[9];               // lane x: node x, lane y: node x + 1
   const typename S::T *row = sp + StageCfg<S>::A + c;
-  S::ld2(row, dA[0], dB[0]);
-  S::ld2(row + 2 * PL, dA[2], dB[2]);
-  S::ld2(row + 4 * PL, dA[4], dB[4]);
-  dA[1] = S::ld1(row + 1 * PL - 1); dB[1] = S::ld1(row + 1 * PL);
-  dA[5] = S::ld1(row + 5 * PL - 1); dB[5] = S::ld1(row + 5 * PL);
-  dA[8] = S::ld1(row + 8 * PL - 1); dB[8] = S::ld1(row + 8 * PL);
-  dA[3] = S::ld1(row + 3 * PL + 1); dB[3] = S::ld1(row + 3 * PL + 2);
-  dA[6] = S::ld1(row + 6 * PL + 1); dB[6] = S::ld1(row + 6 * PL + 2);
-  dA[7] = S::ld1(row + 7 * PL + 1); dB[7] = S::ld1(row + 7 * PL + 2);
-  const NodeState nA = node_state(dA, m.x, m.y, a);
-  collide<S::kHiLo>(dA, nA, a);
-  const NodeState nB = node_state(dB, m.z, m.w, a);
-  collide<S::kHiLo>(dB, nB, a);
+  // e_x = 0 directions as one vector read per plane
+  S::ld2(row, d[0].x, d[0].y);
+  S::ld2(row + 2 * PL, d[2].x, d[2].y);
+  S::ld2(row + 4 * PL, d[4].x, d[4].y);
+  d[1] = make_float2(S::ld1(row + 1 * PL - 1), S::ld1(row + 1 * PL));
+  d[5] = make_float2(S::ld1(row + 5 * PL - 1), S::ld1(row + 5 * PL));
+  d[8] = make_float2(S::ld1(row + 8 * PL - 1), S::ld1(row + 8 * PL));
+  d[3] = make_float2(S::ld1(row + 3 * PL + 1), S::ld1(row + 3 * PL + 2));
+  d[6] = make_float2(S::ld1(row + 6 * PL + 1), S::ld1(row + 6 * PL + 2));
+  d[7] = make_float2(S::ld1(row + 7 * PL + 1), S::ld1(row + 7 * PL + 2));
+  const NodeStateT<float2> n = node_state_t<float2>(d, make_float2(m.x, m.z),
+                                                    make_float2(m.y, m.w), a);
+  collide_t<S::kHiLo>(d, n, a);
   const long long o = (long long)y * a.pitch + x;
   const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
 #pragma unroll
   for (int i = 0; i < 9; ++i)  // 32 random bits per direction and pair
-    S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? pair_bits(h, i) : 0u, 0u);
+    S::template st2<SR>(fout + i * a.plane + o, d[i].x, d[i].y, SR ? pair_bits(h, i) : 0u, 0u);
+}
+
+// The column-edge pairs of a tile: x = 0 and the last pair start
+// (nx - 1) & ~1 of every row the tile touches (tile start (xT, yT), rows
+// below y_end), for a consumer loop that skips them.  The pass hands them
+// out one per thread, so that the long edge path runs in one or two warps
+// per tile instead of diverging inside most of the interior warps when rows
+// are short (the batched kernel: rows of 256 - 1024 nodes; with rows longer
+// than a tile the single-lattice kernel keeps its edges in the loop, where
+// they cost no registers).  Item k (row yT + k / 2, column end k % 2) goes
+// to consumer thread (k + 32 rot) mod (consumer threads): rot turns with
+// the tile, so that no warp is the slow one of every stage.
+template <class S, bool SR>
+__device__ __forceinline__ void staged_column_edges(const typename S::T *__restrict__ sp,
+                                                    const typename S::T *__restrict__ fin,
+                                                    typename S::T *__restrict__ fout,
+                                                    const float2 *__restrict__ med,
+                                                    const StepArgs &a, const float2 *sm, int xT,
+                                                    int yT, int y_end, uint32_t ts, int rot) {
+  constexpr int kThreads = kConsumerWarps * 32;
+  const int k = (threadIdx.x + kThreads - 32 * rot) % kThreads;
+  const int r = k >> 1;
+  const int xl = (a.nx - 1) & ~1;
+  const int x = (k & 1) ? xl : 0;
+  if ((k & 1) && xl == 0) return;  // a row of one pair has one edge pair
+  const int y = yT + r;
+  if (y >= y_end) return;
+  const long long c = (long long)r * a.pitch + x - xT;  // position in the tile
+  if (c < 0 || c >= StageCfg<S>::W) return;
+  const float4 m = *reinterpret_cast<const float4 *>(sm + c);
+  staged_edge_pair<S, SR>(sp, fin, fout, med, a, (int)c, x, y, m, ts);
 }
 
 // ------------------------------------------------------------------ kernel

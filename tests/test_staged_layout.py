@@ -117,6 +117,36 @@ def replay(nx, ny, walls, store, grids=(1, 7, 152)):
                 if xT >= pitch:
                     xT -= pitch
                     yT += 1
+    # the column-edge pass: consumer thread k takes row yT + k // 2, pair x = 0
+    # (k even) or x = (nx - 1) & ~1 (k odd); with the consumer loop, which
+    # skips those pairs, every pair of every tile is updated exactly once
+    xl = (nx - 1) & ~1
+    for t in range(ntiles):
+        T0 = F0 + t * W
+        yT, xT = divmod(T0, pitch)
+        done = []
+        for k in range(cw * 32):
+            r, x = k >> 1, (xl if k & 1 else 0)
+            if (k & 1) and xl == 0:
+                continue
+            y = yT + r
+            if y >= y0 + rows:
+                continue
+            cc = r * pitch + x - xT
+            if cc < 0 or cc >= W:
+                continue
+            assert cc % 2 == 0 and (cc * 8) % 16 == 0
+            done.append((y, x))
+        for cc in range(0, W, 2):
+            p = T0 + cc
+            y, x = divmod(p, pitch)
+            if y >= y0 + rows or x >= nx:
+                continue
+            if x == 0 or x + 2 >= nx:
+                continue  # left to the pass
+            done.append((y, x))
+        want = [divmod(p, pitch) for p in range(T0, min(T0 + W, Fend), 2) if p % pitch < nx]
+        assert sorted(done) == sorted(want)
     # consumer thread mapping covers each tile node pair exactly once
     per = W // 2 // (cw * 32)
     seen = set()
