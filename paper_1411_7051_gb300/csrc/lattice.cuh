@@ -419,7 +419,8 @@ __device__ __forceinline__ void collide(float d[9], const NodeState &s, const St
 
 // Deviation of the porous equilibrium (Eq. 14) from w_i rho0, physical
 // units: deq_i = w_i (rho - rho0) + w_i rho (3 e.u + (9/2 (e.u)^2 - 3/2 u^2)
-// / eps); eps = 0 keeps only w_i (rho - rho0).
+// / eps); eps = 0 keeps only w_i (rho - rho0).  Every multiply-add is an
+// explicit fmaf, so the pressure columns of every kernel round alike.
 __device__ __forceinline__ void equilibrium_dev(float drho, float rho, float ux, float uy,
                                                 float eps, float deq[9]) {
   const float inv_eps = (eps > 0.0f) ? 1.0f / eps : 0.0f;
@@ -431,14 +432,14 @@ __device__ __forceinline__ void equilibrium_dev(float drho, float rho, float ux,
   const float dr1 = kW1 * drho, dr2 = kW2 * drho;
   deq[0] = fmaf(kW0 * rho, -usq, kW0 * drho);
   float eu;
-  eu = vx;        deq[1] = fmaf(r1, 3.0f * eu + fmaf(q * eu, eu, -usq), dr1);
-  eu = vy;        deq[2] = fmaf(r1, 3.0f * eu + fmaf(q * eu, eu, -usq), dr1);
-  eu = -vx;       deq[3] = fmaf(r1, 3.0f * eu + fmaf(q * eu, eu, -usq), dr1);
-  eu = -vy;       deq[4] = fmaf(r1, 3.0f * eu + fmaf(q * eu, eu, -usq), dr1);
-  eu = vx + vy;   deq[5] = fmaf(r2, 3.0f * eu + fmaf(q * eu, eu, -usq), dr2);
-  eu = vy - vx;   deq[6] = fmaf(r2, 3.0f * eu + fmaf(q * eu, eu, -usq), dr2);
-  eu = -vx - vy;  deq[7] = fmaf(r2, 3.0f * eu + fmaf(q * eu, eu, -usq), dr2);
-  eu = vx - vy;   deq[8] = fmaf(r2, 3.0f * eu + fmaf(q * eu, eu, -usq), dr2);
+  eu = vx;        deq[1] = fmaf(r1, fmaf(3.0f, eu, fmaf(q * eu, eu, -usq)), dr1);
+  eu = vy;        deq[2] = fmaf(r1, fmaf(3.0f, eu, fmaf(q * eu, eu, -usq)), dr1);
+  eu = -vx;       deq[3] = fmaf(r1, fmaf(3.0f, eu, fmaf(q * eu, eu, -usq)), dr1);
+  eu = -vy;       deq[4] = fmaf(r1, fmaf(3.0f, eu, fmaf(q * eu, eu, -usq)), dr1);
+  eu = vx + vy;   deq[5] = fmaf(r2, fmaf(3.0f, eu, fmaf(q * eu, eu, -usq)), dr2);
+  eu = vy - vx;   deq[6] = fmaf(r2, fmaf(3.0f, eu, fmaf(q * eu, eu, -usq)), dr2);
+  eu = -vx - vy;  deq[7] = fmaf(r2, fmaf(3.0f, eu, fmaf(q * eu, eu, -usq)), dr2);
+  eu = vx - vy;   deq[8] = fmaf(r2, fmaf(3.0f, eu, fmaf(q * eu, eu, -usq)), dr2);
 }
 
 // Pressure column (non-equilibrium extrapolation, Guo, Zheng & Shi 2002),
