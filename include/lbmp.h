@@ -325,6 +325,26 @@ lbmp_status lbmp_batch_populations(lbmp_batch *b, int32_t i, double *f, int32_t 
  * batch, keep the fastest, restore the populations and time level.  Returns
  * the chosen candidate index and its time per step (either may be NULL). */
 lbmp_status lbmp_batch_tune(lbmp_batch *b, int32_t steps, int32_t *chosen, double *ms_per_step);
+/* Autotuner with a cache.  The shape tuned for a batch is reused, without
+ * timing, by every later batch of the same class (lbmp_batch_class): from
+ * this process's cache, else from the file named by the environment
+ * variable LBMP_TUNE_CACHE (lines "key shape ms_per_step", the last line of a
+ * key wins).  On a miss it runs lbmp_batch_tune and stores the choice (and
+ * appends it to that file).  *from_cache = 1 when nothing was timed; any of
+ * the outputs may be NULL.  Cache file errors are ignored.  Errors: those of
+ * lbmp_batch_tune on a miss. */
+lbmp_status lbmp_batch_tune_cached(lbmp_batch *b, int32_t steps, int32_t *chosen,
+                                   double *ms_per_step, int32_t *from_cache);
+/* Empty this process's shape cache (the file is left as it is). */
+lbmp_status lbmp_batch_tune_cache_clear(void);
+/* Class of a batch, as the cache keys it: storage and FP16 rounding,
+ * boundary kinds, Forchheimer, the node-weighted median of ceil(log2 nx)
+ * over the instances, floor(log2 of all nx*ny nodes), and nsm (the SM count
+ * of the device).  Writes a NUL-terminated key of at most 64 bytes into
+ * key[0..cap).  Host only, touches no device.  Errors: EINVAL for NULL
+ * pointers, count < 1, nsm < 1, a size < 1 or cap too small. */
+lbmp_status lbmp_batch_class(const lbmp_params *p, int32_t count, const int32_t *nx,
+                             const int32_t *ny, int32_t nsm, char *key, int32_t cap);
 /* Use launch candidate `shape` (0 <= shape < the number of candidates, as
  * lbmp_batch_tune reports them; the last one is the staged bulk-copy
  * kernel).  Errors: EINVAL. */

@@ -17,7 +17,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -638,9 +641,98 @@ bool all_fields(const lbmp_batch *b) {
   return true;
 }
 
+// ------------------------------------------------------ tuned-shape cache
+// The launch shape tuned for one batch serves every later batch of the same
+// class: storage and rounding, boundary kinds, Forchheimer, the node-weighted
+// median of ceil(log2 nx) over the instances, floor(log2 of all nodes), and
+// the SM count of the device.  Kept per process, and in the file named by
+// LBMP_TUNE_CACHE when that is set (one "key shape ms_per_step" line per
+// tuning; the last line of a key wins).  File errors are ignored: the cache
+// only saves tuning time.
+std::string class_key(const lbmp_params &p, int count, const int32_t *nx, const int32_t *ny,
+                      int nsm) {
+  std::vector<std::pair<int, long long>> cls;  // (ceil(log2 nx), nodes)
+  long long total = 0;
+  for (int i = 0; i < count; ++i) {
+    int c = 0;
+    while ((1LL << c) < (long long)nx[i]) ++c;
+    const long long n = (long long)nx[i] * ny[i];
+    cls.push_back({c, n});
+    total += n;
+  }
+  std::sort(cls.begin(), cls.end());
+  int med = cls.back().first;
+  long long acc = 0;
+  for (const auto &q : cls) {
+    acc += q.second;
+    if (2 * acc >= total) {
+      med = q.first;
+      break;
+    }
+  }
+  int tcls = 0;  // floor(log2 total)
+  while ((2LL << tcls) <= total) ++tcls;
+  const int sr = p.storage == LBMP_STORE_FP16 && p.fp16_rounding == LBMP_ROUND_STOCHASTIC;
+  char buf[128];
+  snprintf(buf, sizeof(buf), "s%d-r%d-x%d-y%d-f%d-n%d-t%d-m%d", (int)p.storage, sr, (int)p.bc_x,
+           (int)p.bc_y, p.forchheimer ? 1 : 0, med, tcls, nsm);
+  return buf;
+}
+
+struct TuneEntry {
+  int shape;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune_cache;
+
+bool tune_file_lookup(const std::string &key, TuneEntry *out) {
+  const char *path = getenv("LBMP_TUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  char k[128];
+  int shape;
+  double ms;
+  bool found = false;
+  while (fscanf(f, "%127s %d %lf", k, &shape, &ms) == 3)
+    if (key == k && shape >= 0 && shape < lbmp::kNumShapes) {
+      *out = {shape, ms};
+      found = true;
+    }
+  fclose(f);
+  return found;
+}
+
+void tune_file_append(const std::string &key, const TuneEntry &e) {
+  const char *path = getenv("LBMP_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %.9g\n", key.c_str(), e.shape, e.ms);
+  fclose(f);
+}
+
 }  // namespace
 
 extern "C" {
+
+lbmp_status lbmp_batch_class(const lbmp_params *p, int32_t count, const int32_t *nx,
+                             const int32_t *ny, int32_t nsm, char *key, int32_t cap) {
+  try {
+    if (!p || !nx || !ny || !key) return bfail(LBMP_EINVAL, "lbmp_batch_class: NULL argument");
+    if (count < 1) return bfail(LBMP_EINVAL, "count must be >= 1");
+    if (nsm < 1) return bfail(LBMP_EINVAL, "nsm must be >= 1");
+    for (int i = 0; i < count; ++i)
+      if (nx[i] < 1 || ny[i] < 1) return bfail(LBMP_EINVAL, "instance %d: nx, ny must be >= 1", i);
+    const std::string k = class_key(*p, count, nx, ny, nsm);
+    if (cap < (int32_t)k.size() + 1) return bfail(LBMP_EINVAL, "key buffer needs %d bytes", (int)k.size() + 1);
+    memcpy(key, k.c_str(), k.size() + 1);
+    return LBMP_OK;
+  } catch (...) {
+    return bfail(LBMP_EINVAL, "lbmp_batch_class: unexpected exception");
+  }
+}
 
 lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32_t *nx,
                               const int32_t *ny, lbmp_batch **out) {
@@ -904,6 +996,57 @@ lbmp_status lbmp_batch_synchronize(lbmp_batch *b) {
   unsigned err = 0;
   BCK(cudaMemcpy(&err, b->d_err, sizeof(err), cudaMemcpyDeviceToHost));
   if (err) return bfail(LBMP_ETIMEOUT, "a bounded wait of the staged batched kernel gave up");
+  return LBMP_OK;
+}
+
+lbmp_status lbmp_batch_tune_cached(lbmp_batch *b, int32_t steps, int32_t *chosen,
+                                   double *ms_per_step, int32_t *from_cache) {
+  try {
+    if (!b) return bfail(LBMP_EINVAL, "NULL batch");
+    if (steps < 1) return bfail(LBMP_EINVAL, "steps must be >= 1");
+    std::vector<int32_t> nx(b->count), ny(b->count);
+    for (int i = 0; i < b->count; ++i) {
+      nx[i] = b->h_inst[i].a.nx;
+      ny[i] = b->h_inst[i].a.ny;
+    }
+    const std::string key = class_key(b->p, b->count, nx.data(), ny.data(), b->nsm);
+    TuneEntry e{};
+    bool hit;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      hit = it != g_tune_cache.end();
+      if (hit) e = it->second;
+      if (!hit && tune_file_lookup(key, &e)) {
+        g_tune_cache[key] = e;
+        hit = true;
+      }
+    }
+    if (hit) {
+      const lbmp_status st = set_shape(b, e.shape);
+      if (st) return st;
+    } else {
+      int32_t c = 0;
+      double ms = 0.0;
+      const lbmp_status st = lbmp_batch_tune(b, steps, &c, &ms);
+      if (st) return st;
+      e = {c, ms};
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = e;
+      tune_file_append(key, e);
+    }
+    if (chosen) *chosen = e.shape;
+    if (ms_per_step) *ms_per_step = e.ms;
+    if (from_cache) *from_cache = hit ? 1 : 0;
+    return LBMP_OK;
+  } catch (...) {
+    return bfail(LBMP_ECUDA, "lbmp_batch_tune_cached: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_batch_tune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
   return LBMP_OK;
 }
 

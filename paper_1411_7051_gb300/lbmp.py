@@ -166,6 +166,13 @@ def load(path: str = LIB_PATH):
     L.lbmp_batch_populations.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
     L.lbmp_batch_tune.restype = st
     L.lbmp_batch_tune.argtypes = [_VP, ctypes.c_int32, I32P, _D]
+    L.lbmp_batch_tune_cached.restype = st
+    L.lbmp_batch_tune_cached.argtypes = [_VP, ctypes.c_int32, I32P, _D, I32P]
+    L.lbmp_batch_tune_cache_clear.restype = st
+    L.lbmp_batch_tune_cache_clear.argtypes = []
+    L.lbmp_batch_class.restype = st
+    L.lbmp_batch_class.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, I32P, I32P,
+                                   ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32]
     L.lbmp_batch_set_shape.restype = st
     L.lbmp_batch_set_shape.argtypes = [_VP, ctypes.c_int32]
     L.lbmp_batch_get_info.restype = st
@@ -485,6 +492,24 @@ def ka_from_fields(sim: "Sim", log_k, eps, kn, nsteps: int, every: int = 0):
     return _ka_function().apply(log_k, eps, sim, kn, nsteps, every)
 
 
+def batch_class(cfg: SimConfig, sizes, nsm: int) -> str:
+    """``lbmp_batch_class``: the key under which the batch autotuner caches
+    the launch shape of a batch of ``sizes`` [(nx, ny), ...] with the physics
+    of ``cfg`` on a device of ``nsm`` SMs (host only)."""
+    sizes = [(int(nx), int(ny)) for nx, ny in sizes]
+    nx = (ctypes.c_int32 * len(sizes))(*[s[0] for s in sizes])
+    ny = (ctypes.c_int32 * len(sizes))(*[s[1] for s in sizes])
+    buf = ctypes.create_string_buffer(128)
+    prm = cfg.to_params(None)
+    _check(load().lbmp_batch_class(ctypes.byref(prm), len(sizes), nx, ny, int(nsm), buf, 128))
+    return buf.value.decode()
+
+
+def batch_tune_cache_clear():
+    """``lbmp_batch_tune_cache_clear``: forget this process's tuned shapes."""
+    _check(load().lbmp_batch_tune_cache_clear())
+
+
 class Batch:
     """Many lattices advanced together (``lbmp_batch``): ``sizes`` is a list
     of (nx, ny); the physics of ``cfg`` is shared (its nx, ny are ignored)."""
@@ -561,6 +586,15 @@ class Batch:
         ms = ctypes.c_double()
         _check(load().lbmp_batch_tune(self._h, int(steps), ctypes.byref(chosen), ctypes.byref(ms)))
         return chosen.value, ms.value
+
+    def tune_cached(self, steps: int = 10):
+        """``lbmp_batch_tune_cached``: (chosen shape, ms per step, from_cache)."""
+        chosen = ctypes.c_int32()
+        ms = ctypes.c_double()
+        hit = ctypes.c_int32()
+        _check(load().lbmp_batch_tune_cached(self._h, int(steps), ctypes.byref(chosen),
+                                             ctypes.byref(ms), ctypes.byref(hit)))
+        return chosen.value, ms.value, bool(hit.value)
 
     def set_shape(self, shape: int):
         """``lbmp_batch_set_shape``: use launch candidate ``shape``."""

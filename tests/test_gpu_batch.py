@@ -136,3 +136,45 @@ def test_batch_state_errors():
     with pytest.raises(lbmp.LbmpError) as ei:
         lbmp.Batch(cfg, [(64, 40), (2, 10)])   # pressure columns need nx >= 3
     assert ei.value.status == lbmp.EINVAL
+
+
+def test_tune_cache_reuses_shapes_per_class(tmp_path, monkeypatch):
+    """lbmp_batch_tune_cached: a second batch of the same class takes the
+    tuned shape without timing, from the process cache or from the
+    LBMP_TUNE_CACHE file; another class is tuned afresh."""
+    import torch
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("LBMP_TUNE_CACHE", str(path))
+    lbmp.batch_tune_cache_clear()
+    cfg = _cfg(lbmp.STORE_FP32)
+    meds = _media()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def make(sizes, media_list, c=cfg):
+        b = lbmp.Batch(c, sizes)
+        for j, m in enumerate(media_list):
+            b.set_fields(j, m.eps, m.k_i, m.kn)
+        return b
+
+    with make(SIZES, meds) as b:
+        c1, ms1, hit1 = b.tune_cached(2)
+        assert not hit1 and 0 <= c1 < NSHAPES and ms1 > 0
+        c2, ms2, hit2 = b.tune_cached(2)
+        assert hit2 and (c2, ms2) == (c1, ms1)
+    key, shape, _ = path.read_text().split()
+    assert key == lbmp.batch_class(cfg, SIZES, nsm) and int(shape) == c1
+    # the process cache is gone; the file still knows this class (instance
+    # order does not change the class)
+    lbmp.batch_tune_cache_clear()
+    with make(SIZES[::-1], meds[::-1]) as b:
+        c3, _, hit3 = b.tune_cached(2)
+        assert hit3 and c3 == c1
+        # the chosen shape is in use and steps as usual
+        b.step(3)
+        b.synchronize()
+    # another class (FP16 storage) is tuned, and appended to the file
+    with make(SIZES, meds, _cfg(lbmp.STORE_FP16, lbmp.ROUND_NEAREST)) as b:
+        _, _, hit4 = b.tune_cached(2)
+        assert not hit4
+    assert len(path.read_text().splitlines()) == 2
+    lbmp.batch_tune_cache_clear()
