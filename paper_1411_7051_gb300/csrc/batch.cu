@@ -141,18 +141,36 @@ struct TileHead {
 };
 constexpr int kHeadBytes = 128;
 static_assert(sizeof(TileHead) <= kHeadBytes && sizeof(TileHead) % 16 == 0, "tile header");
+// Stage configuration of the batched kernel.  Its consumers hold more per
+// tile (the instance's buffers, geometry and scale) than the single-lattice
+// ones; 12 consumer warps (13 with the producer: 128 registers a thread)
+// keep them in registers, where 16 would spill (FP16 on 512 instances:
+// 124 GLUPS against 117).
+template <class S>
+struct BatchCfg;
+template <>
+struct BatchCfg<StoreF32> : StageCfg<StoreF32> {};
+template <>
+struct BatchCfg<StoreF16> {
+  static constexpr int W = 2304, H = 1, A = 8, STAGES = 3;
+  static constexpr int WARPS = 12;
+};
+template <class S>
+constexpr int batch_threads() {
+  return (BatchCfg<S>::WARPS + 1) * 32;
+}
 template <class S>
 constexpr int batch_smem_bytes() {
-  return StageLayout<S>::kSmemBytes + StageCfg<S>::STAGES * kHeadBytes;
+  return StageLayout<S, BatchCfg<S>>::kSmemBytes + BatchCfg<S>::STAGES * kHeadBytes;
 }
 
 template <class S, bool SR>
-__global__ void __launch_bounds__(kStagedThreads, 1)
+__global__ void __launch_bounds__(batch_threads<S>(), 1)
     batch_staged_kernel(const StepArgs base, const BatchInst *__restrict__ inst,
                         const int4 *__restrict__ tiles, int ntiles, int parity,
                         const unsigned long long *__restrict__ tctr, int k, unsigned *err) {
-  using L = StageLayout<S>;
-  using C = StageCfg<S>;
+  using C = BatchCfg<S>;
+  using L = StageLayout<S, C>;
   using T = typename S::T;
   constexpr int W = C::W, A = C::A, NS = C::STAGES, RW = L::RW;
   constexpr uint32_t kPlaneBytes = (uint32_t)(RW * sizeof(T));
@@ -164,12 +182,12 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(full(s), 1);
-      mbar_init(empty(s), kConsumerWarps);
+      mbar_init(empty(s), C::WARPS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (warp == kConsumerWarps) {
+  if (warp == C::WARPS) {
     // ------------------------------------------------------- producer
     int it = 0;
     bool ok = true;
@@ -242,7 +260,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const unsigned long long tl = *tctr + (unsigned long long)k;
     ts = mix32((uint32_t)tl * 0x9e3779b9u ^ base.seed_lo ^ mix32((uint32_t)(tl >> 32) ^ base.seed_hi));
   }
-  constexpr int kPairs = (W / 2) / (kConsumerWarps * 32);
+  constexpr int kPairs = (W / 2) / (C::WARPS * 32);
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
     const int s = it % NS;
@@ -264,7 +282,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const uint32_t tsi = SR ? ts ^ h.mix : 0u;
 #pragma unroll 1
     for (int j = 0; j < kPairs; ++j) {
-      const int c = 2 * (threadIdx.x + j * kConsumerWarps * 32);
+      const int c = 2 * (threadIdx.x + j * C::WARPS * 32);
       int x = h.x + c, y = h.y;
       while (x >= a.pitch) {
         x -= a.pitch;
@@ -274,13 +292,13 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
       if (x == 0 || x + 2 >= a.nx) continue;  // column edges: the pass below
       const float4 m = *reinterpret_cast<const float4 *>(sm + c);
       if (a.walls && (y == 1 || y == a.ny - 2)) {
-        staged_edge_pair<S, SR>(sp, fin, fout, med, a, c, x, y, m, tsi);
+        staged_edge_pair<S, SR, C>(sp, fin, fout, med, a, c, x, y, m, tsi);
         continue;
       }
-      staged_interior_pair<S, SR>(sp, fout, a, c, x, y, m, tsi);
+      staged_interior_pair<S, SR, C>(sp, fout, a, c, x, y, m, tsi);
     }
-    staged_column_edges<S, SR>(sp, fin, fout, med, a, sm, h.x, h.y, h.y_end, tsi,
-                               it % kConsumerWarps);
+    staged_column_edges<S, SR, C>(sp, fin, fout, med, a, sm, h.x, h.y, h.y_end, tsi,
+                                  it % C::WARPS);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty(s));
   }
@@ -297,14 +315,18 @@ static cudaError_t launch_batch_staged_t(const StepArgs &base, const BatchInst *
   if (attr != cudaSuccess) return attr;
   if (ntiles <= 0) return cudaSuccess;
   const int grid = ntiles < nsm ? ntiles : nsm;
-  batch_staged_kernel<S, SR><<<grid, kStagedThreads, batch_smem_bytes<S>(), s>>>(
+  batch_staged_kernel<S, SR><<<grid, batch_threads<S>(), batch_smem_bytes<S>(), s>>>(
       base, inst, tiles, ntiles, parity, tctr, k, err);
   return cudaGetLastError();
 }
 
 // Tile width of the staged kernel for a storage kind.
 inline int staged_tile_width(int storage) {
-  return storage == LBMP_STORE_FP32 ? StageCfg<StoreF32>::W : StageCfg<StoreF16>::W;
+  return storage == LBMP_STORE_FP32 ? BatchCfg<StoreF32>::W : BatchCfg<StoreF16>::W;
+}
+// Consumer warps of the staged kernel for a storage kind.
+inline int staged_warps(int storage) {
+  return storage == LBMP_STORE_FP32 ? BatchCfg<StoreF32>::WARPS : BatchCfg<StoreF16>::WARPS;
 }
 
 // Per-instance reductions: block partials over the work list (one 256-node
@@ -1215,8 +1237,9 @@ lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out) {
   const lbmp::Shape sh = lbmp::kShapes[b->shape];
   if (sh.persistent == 2) {  // staged: consumer threads and nodes per thread per tile
     const int W = lbmp::staged_tile_width(b->p.storage);
-    out->shape_threads = lbmp::kConsumerWarps * 32;
-    out->shape_nodes_per_thread = W / (lbmp::kConsumerWarps * 32);
+    const int warps = lbmp::staged_warps(b->p.storage);
+    out->shape_threads = warps * 32;
+    out->shape_nodes_per_thread = W / (warps * 32);
   } else {
     out->shape_threads = sh.bx;
     out->shape_nodes_per_thread = sh.npt;

@@ -40,15 +40,19 @@ struct StageCfg;
 template <>
 struct StageCfg<StoreF32> {
   static constexpr int W = 1024, H = 1, A = 4, STAGES = 4;
+  static constexpr int WARPS = kConsumerWarps;
 };
 template <>
 struct StageCfg<StoreF16> {
   static constexpr int W = 2048, H = 1, A = 8, STAGES = 4;
+  static constexpr int WARPS = kConsumerWarps;
 };
 
-template <class S>
+// Shared-memory layout of a stage configuration Cfg (tile width W, halo A,
+// STAGES, WARPS consumer warps).
+template <class S, class Cfg = StageCfg<S>>
 struct StageLayout {
-  using C = StageCfg<S>;
+  using C = Cfg;
   using T = typename S::T;
   static constexpr int RW = C::W + 2 * C::A;  // stage row length (elements)
   static constexpr int kPopBytes = 9 * C::H * RW * (int)sizeof(T);
@@ -60,7 +64,7 @@ struct StageLayout {
   static_assert(RW * (int)sizeof(T) % 16 == 0, "16-byte row alignment");
   static_assert(C::A * (int)sizeof(T) == 16, "halo of 16 bytes");
   static_assert(2 * C::STAGES * 8 <= kBarBytes, "barrier area");
-  static_assert((C::H * C::W / 2) % (kConsumerWarps * 32) == 0, "node pairs per consumer thread");
+  static_assert((C::H * C::W / 2) % (C::WARPS * 32) == 0, "node pairs per consumer thread");
   static_assert(C::H == 1, "tiles are spans of the flattened lattice");
   static_assert(C::W % 64 == 0, "tile starts stay 16-byte aligned");
   static_assert(C::W % 2 == 0 && C::A % 2 == 0, "pairs stay aligned");
@@ -119,13 +123,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 
 // --------------------------------------------------------------- helpers
 // Post-stream values of node (x, y) at tile position (r, c), stored units.
-template <class S>
+template <class S, class Cfg = StageCfg<S>>
 __device__ __forceinline__ void pull_staged(const typename S::T *__restrict__ sp,
                                             const typename S::T *__restrict__ fin,
                                             const StepArgs &a, int r, int c, int x, int y,
                                             float d[9]) {
-  using L = StageLayout<S>;
-  using C = StageCfg<S>;
+  using L = StageLayout<S, Cfg>;
+  using C = Cfg;
   constexpr int RW = L::RW, A = C::A, H = C::H;
   const typename S::T *row[9];
 #pragma unroll
@@ -183,7 +187,7 @@ __device__ __forceinline__ uint32_t pair_bits(uint32_t h, int i) {
 
 // Pressure column xb (0 or nx - 1) at tile position c: non-equilibrium
 // extrapolation from the neighbouring interior node (stage position cn).
-template <class S>
+template <class S, class Cfg = StageCfg<S>>
 __device__ __forceinline__ void staged_pressure(const typename S::T *__restrict__ sp,
                                                 const typename S::T *__restrict__ fin,
                                                 const float2 *__restrict__ med, const StepArgs &a,
@@ -191,7 +195,7 @@ __device__ __forceinline__ void staged_pressure(const typename S::T *__restrict_
   const int xn = (xb == 0) ? 1 : a.nx - 2;
   const float2 mn = med[(long long)y * a.pitch + xn];
   float dn[9];
-  pull_staged<S>(sp, fin, a, 0, cn, xn, y, dn);
+  pull_staged<S, Cfg>(sp, fin, a, 0, cn, xn, y, dn);
   const NodeState sn = node_state(dn, mn.x, mn.y, a);
   const float drho_b = (xb == 0) ? a.drho_in : a.drho_out;
   float eq_b[9], eq_n[9];
@@ -207,7 +211,7 @@ __device__ __forceinline__ void staged_pressure(const typename S::T *__restrict_
 // row; keeping them out of line keeps the interior path's registers and
 // code lean.  The step arguments come by value: taking the address of the
 // kernel parameter would move every read of it to local memory.
-template <class S, bool SR>
+template <class S, bool SR, class Cfg = StageCfg<S>>
 __device__ __noinline__ void staged_edge_pair(const typename S::T *__restrict__ sp,
                                               const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout,
@@ -215,11 +219,12 @@ __device__ __noinline__ void staged_edge_pair(const typename S::T *__restrict__ 
                                               int c, int x, int y, float4 m, uint32_t ts) {
   const bool two = x + 1 < a.nx;
   float dA[9], dB[9];
-  pull_staged<S>(sp, fin, a, 0, c, x, y, dA);
-  if (two) pull_staged<S>(sp, fin, a, 0, c + 1, x + 1, y, dB);
+  pull_staged<S, Cfg>(sp, fin, a, 0, c, x, y, dA);
+  if (two) pull_staged<S, Cfg>(sp, fin, a, 0, c + 1, x + 1, y, dB);
   if (a.pressure) {
-    if (x == 0 || x == a.nx - 1) staged_pressure<S>(sp, fin, med, a, x == 0 ? c + 1 : c - 1, x, y, m.x, dA);
-    if (two && x + 1 == a.nx - 1) staged_pressure<S>(sp, fin, med, a, c, x + 1, y, m.z, dB);
+    if (x == 0 || x == a.nx - 1)
+      staged_pressure<S, Cfg>(sp, fin, med, a, x == 0 ? c + 1 : c - 1, x, y, m.x, dA);
+    if (two && x + 1 == a.nx - 1) staged_pressure<S, Cfg>(sp, fin, med, a, c, x + 1, y, m.z, dB);
   }
   const NodeState nA = node_state(dA, m.x, m.y, a);
   collide<S::kHiLo>(dA, nA, a);
@@ -243,15 +248,15 @@ __device__ __noinline__ void staged_edge_pair(const typename S::T *__restrict__ 
 // neighbour) at tile position c: every source is in the stage.  The pair is
 // computed in the two lanes of float2 values (packed FP32 arithmetic); each
 // lane gives the bits of the one-node update.
-template <class S, bool SR>
+template <class S, bool SR, class Cfg = StageCfg<S>>
 __device__ __forceinline__ void staged_interior_pair(const typename S::T *__restrict__ sp,
                                                      typename S::T *__restrict__ fout,
                                                      const StepArgs &a, int c, int x, int y,
                                                      float4 m, uint32_t ts) {
-  using L = StageLayout<S>;
+  using L = StageLayout<S, Cfg>;
   constexpr int PL = L::RW;  // elements between planes in a stage
   float2 d[9];               // lane x: node x, lane y: node x + 1
-  const typename S::T *row = sp + StageCfg<S>::A + c;
+  const typename S::T *row = sp + Cfg::A + c;
   // e_x = 0 directions as one vector read per plane
   S::ld2(row, d[0].x, d[0].y);
   S::ld2(row + 2 * PL, d[2].x, d[2].y);
@@ -282,14 +287,14 @@ __device__ __forceinline__ void staged_interior_pair(const typename S::T *__rest
 // they cost no registers).  Item k (row yT + k / 2, column end k % 2) goes
 // to consumer thread (k + 32 rot) mod (consumer threads): rot turns with
 // the tile, so that no warp is the slow one of every stage.
-template <class S, bool SR>
+template <class S, bool SR, class Cfg = StageCfg<S>>
 __device__ __forceinline__ void staged_column_edges(const typename S::T *__restrict__ sp,
                                                     const typename S::T *__restrict__ fin,
                                                     typename S::T *__restrict__ fout,
                                                     const float2 *__restrict__ med,
                                                     const StepArgs &a, const float2 *sm, int xT,
                                                     int yT, int y_end, uint32_t ts, int rot) {
-  constexpr int kThreads = kConsumerWarps * 32;
+  constexpr int kThreads = Cfg::WARPS * 32;
   const int k = (threadIdx.x + kThreads - 32 * rot) % kThreads;
   const int r = k >> 1;
   const int xl = (a.nx - 1) & ~1;
@@ -298,9 +303,9 @@ __device__ __forceinline__ void staged_column_edges(const typename S::T *__restr
   const int y = yT + r;
   if (y >= y_end) return;
   const long long c = (long long)r * a.pitch + x - xT;  // position in the tile
-  if (c < 0 || c >= StageCfg<S>::W) return;
+  if (c < 0 || c >= Cfg::W) return;
   const float4 m = *reinterpret_cast<const float4 *>(sm + c);
-  staged_edge_pair<S, SR>(sp, fin, fout, med, a, (int)c, x, y, m, ts);
+  staged_edge_pair<S, SR, Cfg>(sp, fin, fout, med, a, (int)c, x, y, m, ts);
 }
 
 // ------------------------------------------------------------------ kernel

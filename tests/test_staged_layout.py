@@ -17,17 +17,29 @@ CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                     "paper_1411_7051_gb300", "csrc")
 
 
-def stage_cfg():
+def stage_cfg(kind="single"):
+    """Stage constants of the single-lattice kernel (staged.cuh) or of the
+    batched one (batch.cu; its FP32 configuration is the single one)."""
     text = open(os.path.join(CSRC, "staged.cuh")).read()
+    cw = int(re.search(r"kConsumerWarps = (\d+);", text).group(1))
     out = {}
     for store, elem in (("StoreF32", 4), ("StoreF16", 2)):
         m = re.search(r"struct StageCfg<%s>\s*{\s*static constexpr int W = (\d+), H = (\d+), "
                       r"A = (\d+), STAGES = (\d+);" % store, text)
         assert m, store
         W, H, A, NS = map(int, m.groups())
-        out[store] = dict(W=W, H=H, A=A, NS=NS, elem=elem)
-    cw = int(re.search(r"kConsumerWarps = (\d+);", text).group(1))
-    return out, cw
+        out[store] = dict(W=W, H=H, A=A, NS=NS, elem=elem, warps=cw, head=0)
+    if kind == "batch":
+        btext = open(os.path.join(CSRC, "batch.cu")).read()
+        head = int(re.search(r"kHeadBytes = (\d+);", btext).group(1))
+        m = re.search(r"struct BatchCfg<StoreF16>\s*{\s*static constexpr int W = (\d+), H = (\d+), "
+                      r"A = (\d+), STAGES = (\d+);\s*static constexpr int WARPS = (\d+);", btext)
+        assert m
+        W, H, A, NS, warps = map(int, m.groups())
+        out["StoreF16"] = dict(W=W, H=H, A=A, NS=NS, elem=2, warps=warps, head=head)
+        assert re.search(r"struct BatchCfg<StoreF32> : StageCfg<StoreF32> {};", btext)
+        out["StoreF32"]["head"] = head
+    return out
 
 
 def pitch_of(nx):
@@ -42,16 +54,16 @@ def pitch_of(nx):
 EY = [0, 0, 1, 0, -1, 1, 1, -1, -1]
 
 
-def replay(nx, ny, walls, store, grids=(1, 7, 152)):
-    cfg, cw = stage_cfg()
-    c = cfg[store]
-    W, H, A, NS, elem = c["W"], c["H"], c["A"], c["NS"], c["elem"]
+def replay(nx, ny, walls, store, grids=(1, 7, 152), kind="single"):
+    c = stage_cfg(kind)[store]
+    W, H, A, NS, elem, cw = c["W"], c["H"], c["A"], c["NS"], c["elem"], c["warps"]
     assert H == 1 and W % 64 == 0
     RW = W + 2 * A
     pop_bytes = 9 * RW * elem
     stage_bytes = pop_bytes + W * 8
     bar_bytes = 128
-    assert bar_bytes + NS * stage_bytes <= 227 * 1024
+    assert bar_bytes + NS * stage_bytes + NS * c["head"] <= 227 * 1024
+    assert (bar_bytes + NS * stage_bytes) % 16 == 0  # the batched tile headers follow
     assert 2 * NS * 8 <= bar_bytes
     pitch = pitch_of(nx)
     NP = pitch * ny                      # nodes of a plane (the wrap length)
@@ -160,7 +172,8 @@ def replay(nx, ny, walls, store, grids=(1, 7, 152)):
 @pytest.mark.parametrize("walls", [False, True])
 @pytest.mark.parametrize("nx,ny", [(1, 3), (3, 3), (5, 1), (64, 33), (131, 37), (255, 9), (256, 4),
                                    (257, 5), (513, 17), (1000, 7), (4096, 12), (4099, 6)])
-def test_staged_copies_in_bounds_and_aligned(nx, ny, walls, store):
+@pytest.mark.parametrize("kind", ["single", "batch"])
+def test_staged_copies_in_bounds_and_aligned(nx, ny, walls, store, kind):
     if walls and ny < 3:
         pytest.skip("walls need ny >= 3")
-    replay(nx, ny, walls, store)
+    replay(nx, ny, walls, store, kind=kind)
