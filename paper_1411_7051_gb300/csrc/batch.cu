@@ -163,6 +163,9 @@ template <class S>
 constexpr int batch_smem_bytes() {
   return StageLayout<S, BatchCfg<S>>::kSmemBytes + BatchCfg<S>::STAGES * kHeadBytes;
 }
+static_assert(batch_smem_bytes<StoreF16>() <= 227 * 1024 &&
+                  batch_smem_bytes<StoreF32>() <= 227 * 1024,
+              "stages and tile headers fit the 227 KB of shared memory of a CTA");
 
 template <class S, bool SR>
 __global__ void __launch_bounds__(batch_threads<S>(), 1)
