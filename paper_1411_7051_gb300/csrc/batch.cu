@@ -144,12 +144,16 @@ static_assert(sizeof(TileHead) <= kHeadBytes && sizeof(TileHead) % 16 == 0, "til
 // Stage configuration of the batched kernel.  Its consumers hold more per
 // tile (the instance's buffers, geometry and scale) than the single-lattice
 // ones; 12 consumer warps (13 with the producer: 128 registers a thread)
-// keep them in registers, where 16 would spill (FP16 on 512 instances:
-// 124 GLUPS against 117).
+// keep them in registers, where 16 would spill, and each thread takes two
+// or three node pairs per tile (on 512 instances: FP16 124 GLUPS against
+// 117, FP32 82 against 73).
 template <class S>
 struct BatchCfg;
 template <>
-struct BatchCfg<StoreF32> : StageCfg<StoreF32> {};
+struct BatchCfg<StoreF32> {
+  static constexpr int W = 1536, H = 1, A = 4, STAGES = 3;
+  static constexpr int WARPS = 12;
+};
 template <>
 struct BatchCfg<StoreF16> {
   static constexpr int W = 2304, H = 1, A = 8, STAGES = 3;

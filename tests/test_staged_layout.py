@@ -19,7 +19,7 @@ CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 
 def stage_cfg(kind="single"):
     """Stage constants of the single-lattice kernel (staged.cuh) or of the
-    batched one (batch.cu; its FP32 configuration is the single one)."""
+    batched one (batch.cu)."""
     text = open(os.path.join(CSRC, "staged.cuh")).read()
     cw = int(re.search(r"kConsumerWarps = (\d+);", text).group(1))
     out = {}
@@ -32,13 +32,13 @@ def stage_cfg(kind="single"):
     if kind == "batch":
         btext = open(os.path.join(CSRC, "batch.cu")).read()
         head = int(re.search(r"kHeadBytes = (\d+);", btext).group(1))
-        m = re.search(r"struct BatchCfg<StoreF16>\s*{\s*static constexpr int W = (\d+), H = (\d+), "
-                      r"A = (\d+), STAGES = (\d+);\s*static constexpr int WARPS = (\d+);", btext)
-        assert m
-        W, H, A, NS, warps = map(int, m.groups())
-        out["StoreF16"] = dict(W=W, H=H, A=A, NS=NS, elem=2, warps=warps, head=head)
-        assert re.search(r"struct BatchCfg<StoreF32> : StageCfg<StoreF32> {};", btext)
-        out["StoreF32"]["head"] = head
+        for store, elem in (("StoreF32", 4), ("StoreF16", 2)):
+            m = re.search(r"struct BatchCfg<%s>\s*{\s*static constexpr int W = (\d+), H = (\d+), "
+                          r"A = (\d+), STAGES = (\d+);\s*static constexpr int WARPS = (\d+);" % store,
+                          btext)
+            assert m, store
+            W, H, A, NS, warps = map(int, m.groups())
+            out[store] = dict(W=W, H=H, A=A, NS=NS, elem=elem, warps=warps, head=head)
     return out
 
 
