@@ -353,10 +353,11 @@ lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out);
 
 /* Global permeability of a lattice state held entirely in caller memory,
  * allocating nothing.  The paper has no counterpart: this serves callers
- * that cannot call cudaMalloc -- code that runs while another component
- * holds the device in a stream capture, processes whose device memory is
- * owned by another framework's pool, latency-bound loops that may not pay
- * for an allocation.  It computes what lbmp_permeability computes (Darcy's
+ * that cannot call cudaMalloc -- processes whose device memory is owned by
+ * another framework's pool (an allocation behind the pool's back can fail or
+ * take memory the pool has budgeted), and latency-bound loops that may not
+ * pay for an allocation or for the device-wide synchronisation of cudaFree.
+ * It computes what lbmp_permeability computes (Darcy's
  * law over the whole domain with eps p = c_s^2 rho for the pressure drop),
  * in FP64, from:
  *   p            lattice size, tau, J, G, boundary kinds, rho0, rho_in,
@@ -376,7 +377,10 @@ lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out);
  * same array: calls that overlap on the GPU (other streams, other threads)
  * race.  The first call on each device looks up the array's device address
  * (once, under a lock); make that first call before any stream capture.
- * Errors: EINVAL (NULL pointer, bad size), ECUDA. */
+ * The sizes of the caller's arrays cannot be checked here: they must hold
+ * what nx and ny imply.
+ * Errors: EINVAL (NULL pointer, a parameter lbmp_create would reject among
+ * those read here, a lattice beyond the scratch), ECUDA. */
 lbmp_status lbmp_permeability_noalloc(const lbmp_params *p, const double *f, const double *eps,
                                       const double *k_i, const double *kn, double *out,
                                       void *stream);

@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(batch_threads<S>(), 1)
         mbar_arrive_expect_tx(full(s), 9u * kPlaneBytes + med_bytes);
       }
       __syncwarp();
+      if (t == base.test_drop_tile) continue;  // the consumers' wait must run out
       const uint32_t st = sbase + (uint32_t)L::kBarBytes + (uint32_t)s * (uint32_t)L::kStageBytes;
       if (lane < 9) {
         const int ey = (lane == 2 || lane == 5 || lane == 6) ? 1
@@ -814,6 +815,8 @@ lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32
     e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) BTRY(bcuda(e, "cudaStreamCreate (capture)"));
     const size_t elem = p.storage == LBMP_STORE_FP32 ? 4 : 2;
+    int drop_tile = -1;
+    if (const char *f = std::getenv("LBMP_TEST_DROP_TILE")) drop_tile = std::atoi(f);
     b->h_inst.resize(count);
     b->fields_set.assign(count, 0);
     b->eps_mean.assign(count, 1.0);
@@ -849,7 +852,9 @@ lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32
       a.forch = p.forchheimer != 0;
       a.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
       a.seed_hi = (uint32_t)(p.seed >> 32);
-      a.test_drop_tile = -1;
+      // instance 0's arguments are the kernel's shared ones: the staged
+      // kernel withholds the copies of that tile (tests of its bounded waits)
+      a.test_drop_tile = i == 0 ? drop_tile : -1;
       a.kn_model = p.kn_model;
       a.kn_beta = 0.0f;
       a.kn0 = nullptr;

@@ -1,10 +1,11 @@
 // Allocation-free global permeability (lbmp_permeability_noalloc).
 //
-// Some callers cannot call cudaMalloc: code running while another component
-// holds the device in a stream capture, processes whose device memory is
-// owned by a pool of another framework that must stay the only allocator,
-// and latency-bound control loops that may not pay for an allocation.  For
-// them this entry point takes every input and output from the caller and
+// Some callers cannot call cudaMalloc: processes whose device memory is
+// owned by a pool of another framework that must stay the only allocator
+// (an allocation behind its back can fail, or take memory the pool has
+// budgeted for itself), and latency-bound control loops that may not pay for
+// an allocation and the device-wide synchronisation of cudaFree.  For them
+// this entry point takes every input and output from the caller and
 // keeps its only scratch -- the per-block FP64 partial sums of the
 // reduction -- in a fixed array in the library's own device memory, which
 // every GPU that loads the library holds until the process exits.
@@ -166,9 +167,16 @@ lbmp_status lbmp_permeability_noalloc(const lbmp_params *p, const double *f, con
   try {
     if (!p || !f || !eps || !k_i || !kn || !out)
       return nfail(LBMP_EINVAL, "lbmp_permeability_noalloc: NULL argument");
-    if (p->nx < 1 || p->ny < 1) return nfail(LBMP_EINVAL, "nx, ny must be >= 1");
-    if (p->ny > 65535) return nfail(LBMP_EINVAL, "ny must be <= 65535");
-    if (!(p->tau > 0.5)) return nfail(LBMP_EINVAL, "tau must be > 0.5");
+    // the checks of lbmp_create on the fields read here (the others are
+    // ignored: they are set to valid values for the check)
+    lbmp_params q = *p;
+    q.storage = LBMP_STORE_FP32;
+    q.kernel = LBMP_KERNEL_DIRECT;
+    q.fp16_log2_scale = 0;
+    q.fp16_rounding = LBMP_ROUND_STOCHASTIC;
+    lbmp_status vst = lbmp::validate_params(&q);  // also fills J = 0, rho0 = 0 with 1
+    if (vst) return vst;
+    p = &q;
     const long long blocks = (long long)((p->nx + kNoallocBX - 1) / kNoallocBX) * p->ny;
     if (blocks > kNoallocMaxBlocks)
       return nfail(LBMP_EINVAL,
@@ -176,8 +184,6 @@ lbmp_status lbmp_permeability_noalloc(const lbmp_params *p, const double *f, con
                    "(ceil(nx / %d) * ny must be <= %d)",
                    p->nx, p->ny, blocks, kNoallocMaxBlocks, kNoallocBX, kNoallocMaxBlocks);
     const int walls = p->bc_y == LBMP_BCY_WALLS, pressure = p->bc_x == LBMP_BCX_PRESSURE;
-    if ((walls && p->ny < 3) || (pressure && p->nx < 3))
-      return nfail(LBMP_EINVAL, "lattice too small for its boundary kinds");
     double *scratch = nullptr;
     lbmp_status st = scratch_for_current_device(&scratch);
     if (st) return st;
@@ -187,13 +193,12 @@ lbmp_status lbmp_permeability_noalloc(const lbmp_params *p, const double *f, con
     a.walls = walls;
     a.pressure = pressure;
     a.forch = p->forchheimer != 0;
-    a.kn_model = p->kn_model == LBMP_KN_FIRST_ORDER ? LBMP_KN_FIRST_ORDER : LBMP_KN_BKC;
+    a.kn_model = p->kn_model;
     a.kn_beta = p->kn_beta;
-    const double J = (p->J == 0.0) ? 1.0 : p->J;
-    a.nu = (p->tau - 0.5) / 3.0 / J;
+    a.nu = (p->tau - 0.5) / 3.0 / p->J;
     a.Gx = p->Gx;
     a.Gy = p->Gy;
-    a.rho0 = (p->rho0 == 0.0) ? 1.0 : p->rho0;
+    a.rho0 = p->rho0;
     a.rho_in = p->rho_in;
     a.rho_out = p->rho_out;
     cudaStream_t s = (cudaStream_t)stream;

@@ -186,6 +186,11 @@ def _check(status: int):
         raise LbmpError(status, load().lbmp_last_error().decode())
 
 
+def last_error() -> str:
+    """``lbmp_last_error``: message of the last error raised on this thread."""
+    return load().lbmp_last_error().decode()
+
+
 def fc(kn: float) -> float:
     """Eq. 6-7 correction factor, evaluated by the library (host code)."""
     return float(load().lbmp_fc(float(kn)))
@@ -230,13 +235,31 @@ def permeability_noalloc(cfg: "SimConfig", f, eps, k_i, kn, out, stream=None):
     """``lbmp_permeability_noalloc``: k_g, <u_x> and the non-finite count of
     a state held in caller device memory, written to ``out`` (3 float64 on
     the device), asynchronously on ``stream`` (a torch.cuda.Stream; default:
-    the current stream).  All tensors: contiguous float64 CUDA tensors, f of
-    shape [9, ny, nx], the medium [ny, nx]."""
+    the current stream).  All tensors: contiguous float64 CUDA tensors on the
+    current device, f with 9 * ny * nx elements, the medium with ny * nx.
+    The C entry point cannot see the sizes of the arrays it is given, so
+    they are checked here, before anything is launched."""
     torch = _torch()
-    for t in (f, eps, k_i, kn, out):
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-                and t.is_contiguous()):
-            raise TypeError("permeability_noalloc takes contiguous float64 CUDA tensors")
+    named = (("f", f), ("eps", eps), ("k_i", k_i), ("kn", kn), ("out", out))
+    for name, t in named:
+        if not (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError(f"permeability_noalloc: {name} must be a contiguous float64 tensor")
+    n = int(cfg.nx) * int(cfg.ny)
+    need = {"f": 9 * n, "eps": n, "k_i": n, "kn": n}
+    for name, t in named[:4]:
+        if t.numel() != need[name]:
+            raise ValueError(f"permeability_noalloc: {name} has {t.numel()} elements, "
+                             f"a {cfg.nx} x {cfg.ny} lattice needs {need[name]}")
+    if out.numel() < 3:
+        raise ValueError("permeability_noalloc: out needs 3 elements")
+    for name, t in named:
+        if not t.is_cuda:
+            raise TypeError(f"permeability_noalloc: {name} must be a CUDA tensor")
+    dev = torch.cuda.current_device()
+    for name, t in named:
+        if t.device.index != dev:
+            raise ValueError(f"permeability_noalloc: {name} is on cuda:{t.device.index}, "
+                             f"the current device is cuda:{dev}")
     if stream is None:
         stream = torch.cuda.current_stream()
     params = cfg.to_params(None)

@@ -73,3 +73,42 @@ def test_null_arguments(L):
     assert L.lbmp_destroy(None) == lbmp.OK
     assert L.lbmp_step(None, 1) == lbmp.EINVAL
     assert L.lbmp_get_info(None, None) == lbmp.EINVAL
+
+
+@pytest.mark.parametrize("kw,needle", [
+    ({"kn_model": 7}, "kn_model"),
+    ({"bc_x": 5}, "bc_x"),
+    ({"bc_y": -1}, "bc_y"),
+    ({"J": -1.0}, "J"),
+    ({"tau": 0.5}, "tau"),
+    ({"bc_x": lbmp.BCX_PRESSURE, "rho_in": 1.01, "rho_out": 0.99, "kn_beta": -200.0},
+     "non-positive pressure"),
+    ({"bc_y": lbmp.BCY_WALLS, "ny": 2}, "ny >= 3"),
+])
+def test_noalloc_rejects_what_create_rejects(L, kw, needle):
+    """lbmp_permeability_noalloc checks the parameters it reads as
+    lbmp_create does, before any CUDA call (the pointers are never used)."""
+    cfg = lbmp.SimConfig(**{"nx": 64, "ny": 32, **kw})
+    p = cfg.to_params(None)
+    dummy = (ctypes.c_double * 4)()
+    ptr = ctypes.cast(dummy, ctypes.c_void_p)
+    st = L.lbmp_permeability_noalloc(ctypes.byref(p), ptr, ptr, ptr, ptr, ptr, None)
+    assert st == lbmp.EINVAL
+    assert needle in lbmp.last_error()
+
+
+def test_noalloc_binding_checks_sizes_first():
+    """The binding checks the sizes the C entry point cannot see before it
+    needs a GPU: arrays one element short raise ValueError."""
+    import torch
+    nx, ny = 16, 8
+    cfg = lbmp.SimConfig(nx, ny)
+    z = lambda n: torch.zeros(n, dtype=torch.float64)   # noqa: E731
+    good = [z(9 * nx * ny), z(nx * ny), z(nx * ny), z(nx * ny), z(3)]
+    for k in range(5):
+        args = list(good)
+        args[k] = z(good[k].numel() - 1)
+        with pytest.raises(ValueError):
+            lbmp.permeability_noalloc(cfg, *args)
+    with pytest.raises(TypeError):   # right sizes, but host tensors
+        lbmp.permeability_noalloc(cfg, *good)

@@ -178,3 +178,75 @@ def test_tune_cache_reuses_shapes_per_class(tmp_path, monkeypatch):
         assert not hit4
     assert len(path.read_text().splitlines()) == 2
     lbmp.batch_tune_cache_clear()
+
+
+# instances shaped like the batched-sweep workload: two-component media
+# (corr. length 32, matrix eps 0.2 / k_i 1e-5, inclusions eps 0.6 / k_i 1e-3),
+# rows of 256 - 1024 nodes, pressure-driven in x, plates in y, Forchheimer on,
+# Kn spread over [1e-3, 10]; heights cut so that the oracle runs in seconds
+SWEEP_SIZES = [(256, 48), (384, 40), (512, 32), (1024, 24)]
+SWEEP_KN = [0.001, 0.1, 1.0, 10.0]
+
+
+def _sweep_media():
+    return [media.two_component(nx, seed=1000 + j, corr_len=32.0, kn=kn, ny=ny)
+            for j, ((nx, ny), kn) in enumerate(zip(SWEEP_SIZES, SWEEP_KN))]
+
+
+@pytest.mark.parametrize("storage", [lbmp.STORE_FP32, lbmp.STORE_FP16])
+def test_batch_staged_against_oracle(orc, storage):
+    """The staged bulk-copy candidate (the shape the tuner picks for the
+    sweep) against the FP64 oracle, instance by instance: FP32 k_g within
+    1e-6, FP16-stored populations with stochastic rounding within 1e-3."""
+    import json
+    import os
+    cfg = _cfg(storage, lbmp.ROUND_STOCHASTIC, tau=0.8, rho_in=1.0005, rho_out=0.9995)
+    meds = _sweep_media()
+    nsteps = 1500
+    with lbmp.Batch(cfg, SWEEP_SIZES) as b:
+        b.set_shape(NSHAPES - 1)
+        assert b.info().persistent == 2
+        for j, m in enumerate(meds):
+            b.set_fields(j, m.eps, m.k_i, m.kn)
+        b.step(nsteps)
+        b.synchronize()
+        kg_b, _ = b.permeability()
+    tol = 1e-6 if storage == lbmp.STORE_FP32 else 1e-3
+    errs = []
+    for j, ((nx, ny), m) in enumerate(zip(SWEEP_SIZES, meds)):
+        o = oracle_sim(orc, Case(nx, ny, tau=0.8, pressure=True, walls=True, rho_in=1.0005,
+                                 rho_out=0.9995, forchheimer=1, medium=m))
+        o.step(nsteps)
+        kg_o, _ = o.permeability()
+        errs.append(abs(kg_b[j] / kg_o - 1))
+    path = os.environ.get("LBMP_PARITY_LOG")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"test": "batch_staged_against_oracle", "storage": storage,
+                                 "e_k": errs}) + "\n")
+    assert max(errs) <= tol, errs
+
+
+def test_batch_staged_bounded_wait_reports_timeout(monkeypatch):
+    """The batched staged kernel's waits are bounded: with the copies of one
+    tile withheld, the consumers give up after their limit, the host reports
+    ETIMEOUT, and a fresh batch runs."""
+    cfg = _cfg(lbmp.STORE_FP16, lbmp.ROUND_STOCHASTIC)
+    meds = _sweep_media()
+    monkeypatch.setenv("LBMP_TEST_DROP_TILE", "3")
+    b = lbmp.Batch(cfg, SWEEP_SIZES)
+    monkeypatch.delenv("LBMP_TEST_DROP_TILE")
+    b.set_shape(NSHAPES - 1)
+    for j, m in enumerate(meds):
+        b.set_fields(j, m.eps, m.k_i, m.kn)
+    b.step(1)
+    with pytest.raises(lbmp.LbmpError) as ei:
+        b.synchronize()
+    assert ei.value.status == lbmp.ETIMEOUT
+    b.close()
+    with lbmp.Batch(cfg, SWEEP_SIZES) as ok:
+        ok.set_shape(NSHAPES - 1)
+        for j, m in enumerate(meds):
+            ok.set_fields(j, m.eps, m.k_i, m.kn)
+        ok.step(5)
+        ok.synchronize()

@@ -1,7 +1,7 @@
 """Dynamic Knudsen number and the first-order Klinkenberg factor on the GPU
 against the FP64 oracle (the tolerances of test_gpu_parity: one FP32 step
-within 2e-9 absolute; FP32 steady states rel-L2(u) <= 1e-5 and k_g <= 1e-6;
-transient pressure-driven states k_g <= 1e-5; FP16 k_g <= 1e-3).
+within 2e-9 absolute; FP32 rel-L2(u) <= 1e-5 and k_g <= 1e-6, steady or
+transient; FP16 k_g <= 1e-3).
 
 With a dynamic Kn a node's apparent permeability is k_i f_c(Kn0 p0 / p)
 at its current pressure p / p0 = 1 + beta (rho - rho0); the GPU evaluates
@@ -97,7 +97,7 @@ def test_two_component_transient(orc, kn):
     for n in (150, 850):
         osim.step(n)
         gs.step(n)
-    _compare(gs, osim, case, rel_u=1e-5, rel_k=1e-5)
+    _compare(gs, osim, case, rel_u=1e-5, rel_k=1e-6)
     # the dynamic Kn changes the answer: against the static run
     static = Case(**{**case.__dict__, "kn_beta": 0.0})
     gst = gpu_sim(static, FP32)

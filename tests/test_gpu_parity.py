@@ -5,13 +5,13 @@ inputs.  Tolerances:
   absolute (FP32 rounding of O(1e-3) deviations and of rho);
 * steady states, FP32: relative L2 of the velocity <= 1e-5 and global
   permeability <= 1e-6 relative;
-* transient states of pressure-driven runs, FP32: relative L2 of the
-  velocity <= 1e-5 and global permeability <= 1e-5.  While the pressure
-  wave crosses the lattice the stored deviations f_i - w_i rho0 carry the
-  density deviation (up to 5e-4), about 1e3 times the velocity signal, so
-  one FP32 rounding (2^-24) moves the velocity of a node by ~1e-4 relative
-  per step; the domain mean averages this to ~1e-6 and the bound keeps a
-  factor 10;
+* transient states of pressure-driven runs, FP32: the same bounds.  While
+  the pressure wave crosses the lattice the stored deviations f_i - w_i rho0
+  carry the density deviation (up to 5e-4), about 1e3 times the velocity
+  signal, so one FP32 rounding (2^-24) moves the velocity of a node by
+  ~1e-4 relative per step.  Exactly conserving collisions and explicitly
+  rounded arithmetic keep these errors zero-mean, and the domain mean of
+  the velocity (k_g) stays within 1e-6;
 * FP16-stored populations (stochastic rounding, the default): global
   permeability <= 1e-3 relative; one step from the same state: each
   population within one FP16 ulp of its deviation (2^-10 relative).
@@ -167,7 +167,7 @@ def test_two_component_fp32(orc, kn):
     for n in (100, 900):
         osim.step(n)
         gs.step(n)
-    _compare_velocity(gs, osim, case, rel_k=1e-5)
+    _compare_velocity(gs, osim, case, rel_k=1e-6)
 
 
 def test_forchheimer_shale_fp32(orc):
@@ -175,7 +175,7 @@ def test_forchheimer_shale_fp32(orc):
     are ~1e-9 under a density deviation of ~1e-3, so FP32 carries them with
     a few significant digits only; the fracture velocities dominate the L2
     norm.  Velocity bound 1e-5 (measured 1.4e-6 with the collision's
-    1 - omega and omega summing to exactly 1), permeability 1e-5."""
+    1 - omega and omega summing to exactly 1), permeability 1e-6."""
     med = media.shale_fractures(n=160, seed=5, n_fractures=4, length=(40, 120))
     case = Case(160, 160, tau=0.9, pressure=True, walls=False, rho_in=1.001,
                 rho_out=0.999, forchheimer=1, medium=med)
@@ -183,7 +183,7 @@ def test_forchheimer_shale_fp32(orc):
     gs = gpu_sim(case, FP32)
     osim.step(600)
     gs.step(600)
-    _compare_velocity(gs, osim, case, rel_u=1e-5, rel_k=1e-5)
+    _compare_velocity(gs, osim, case, rel_u=1e-5, rel_k=1e-6)
 
 
 def test_impermeable_and_open_nodes_fp32(orc):

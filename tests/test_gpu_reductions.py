@@ -1,0 +1,124 @@
+"""The GPU's FP64 reductions other than k_g -- the relative velocity residual
+(||u - u_prev||_2 / ||u||_2 over the fluid nodes, the steady-state test) and
+the total mass (sum of rho over the fluid nodes) -- against the oracle's
+orc_residual / orc_mass.  Global quantities of Section IV.A (Darcy's law
+over the whole domain) rest on these sums.
+
+Two comparisons per case:
+  * same state: the oracle is loaded with the populations the GPU holds and
+    given, as its snapshot, the FP32 velocity the GPU stored at its own
+    snapshot.  What differs is then only the GPU's FP32 velocity arithmetic
+    (~1e-7 relative per node) and the summation order, so the residual
+    (of order 0.1 - 1 here) agrees to 1e-6 relative and the mass, whose
+    per-node FP32 density rounding (~6e-8 of a deviation of ~1e-3) averages
+    out, to 1e-12;
+  * same run: both sides step from rest; the FP32 trajectory drifts from
+    the FP64 one by the velocity bound of the step parity tests (rel-L2 <=
+    1e-5), so the residual agrees to 1e-4 relative and the mass to 1e-9.
+Measured errors are appended to $LBMP_PARITY_LOG when set.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1411_7051_gb300 import media
+from helpers import Case, gpu_sim, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP16 = 0, 1
+
+
+def _log(**kw):
+    path = os.environ.get("LBMP_PARITY_LOG")
+    if path:
+        kw["test"] = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+        with open(path, "a") as fh:
+            fh.write(json.dumps(kw) + "\n")
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _cases():
+    two = media.two_component(128, seed=2, corr_len=16.0, kn=0.1, ny=72)
+    rnd = media.random_medium(97, 45, seed=9, p_open=0.2, p_solid=0.1, log10_k_range=(-2, 1))
+    return {
+        "pressure_walls": Case(128, 72, tau=0.8, pressure=True, walls=True, rho_in=1.0005,
+                               rho_out=0.9995, forchheimer=1, medium=two),
+        "pressure_periodic": Case(128, 72, tau=0.9, pressure=True, walls=False, rho_in=1.001,
+                                  rho_out=0.999, medium=two),
+        "body_walls_open_solid": Case(97, 45, tau=1.1, G=(1e-5, 2e-6), walls=True,
+                                      forchheimer=1, medium=rnd),
+    }
+
+
+@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("name", list(_cases()))
+def test_residual_and_mass_same_state(orc, name, storage):
+    case = _cases()[name]
+    gs = gpu_sim(case, storage)
+    gs.step(150)
+    assert gs.residual() == pytest.approx(1.0, rel=1e-12)   # against the zero snapshot
+    _, ux_a, uy_a = gs.macroscopic()       # the velocity just stored as the snapshot
+    gs.step(150)
+    r_gpu = gs.residual()
+    m_gpu = gs.mass()
+    osim = oracle_sim(orc, case)
+    osim.set_populations(_np(gs.populations()))
+    r_orc = osim.residual(_np(ux_a), _np(uy_a))
+    m_orc = osim.mass()
+    e_r, e_m = abs(r_gpu / r_orc - 1), abs(m_gpu / m_orc - 1)
+    _log(e_residual=e_r, residual=r_gpu, residual_oracle=r_orc, e_mass=e_m,
+         storage="fp32" if storage == FP32 else "fp16")
+    assert 1e-3 < r_orc < 2.0
+    assert e_r <= 1e-6, (r_gpu, r_orc)
+    assert e_m <= 1e-12, (m_gpu, m_orc)
+
+
+@pytest.mark.parametrize("name", list(_cases()))
+def test_residual_and_mass_same_run(orc, name):
+    case = _cases()[name]
+    gs = gpu_sim(case, FP32)
+    osim = oracle_sim(orc, case)
+    gs.residual()
+    _, oux, ouy = osim.macroscopic()
+    assert gs.mass() == pytest.approx(osim.mass(), rel=1e-13, abs=0)   # rest state
+    for n in (200, 300):
+        gs.step(n)
+        osim.step(n)
+        r_gpu = gs.residual()
+        r_orc = osim.residual(oux, ouy)
+        _, oux, ouy = osim.macroscopic()
+        m_gpu, m_orc = gs.mass(), osim.mass()
+        e_r, e_m = abs(r_gpu / r_orc - 1), abs(m_gpu / m_orc - 1)
+        _log(e_residual=e_r, residual=r_gpu, residual_oracle=r_orc, e_mass=e_m, steps=n)
+        assert e_r <= 1e-4, (n, r_gpu, r_orc)
+        assert e_m <= 1e-9, (n, m_gpu, m_orc)
+
+
+def test_steady_channel_residual_tracks_the_oracle(orc):
+    """Validation channel (64 x 33, eps 0.7, Da 1e-3, Kn 0.1, G 1e-6): the
+    residual over 20-step windows (the Darcy damping eps nu / k_a = 0.049 per
+    step shrinks it ~e-fold per window) decays alike on both sides while it
+    is far above the FP32 floor (~1e-7)."""
+    med = media.channel(64, 33, 0.7, 1e-3, 0.1)
+    case = Case(64, 33, tau=0.8, G=(1e-6, 0.0), walls=True, medium=med)
+    gs = gpu_sim(case, FP32)
+    osim = oracle_sim(orc, case)
+    gs.residual()
+    _, oux, ouy = osim.macroscopic()
+    checked = 0
+    for k in range(15):
+        gs.step(20)
+        osim.step(20)
+        r_gpu = gs.residual()
+        r_orc = osim.residual(oux, ouy)
+        _, oux, ouy = osim.macroscopic()
+        if r_orc > 1e-4:
+            assert abs(r_gpu / r_orc - 1) <= 1e-3, (k, r_gpu, r_orc)
+            checked += 1
+    assert checked >= 5

@@ -21,10 +21,10 @@ TAU = 0.8
 NU = (TAU - 0.5) / 3.0
 
 
-def uniform_kg(log_k, eps, nsteps, G, forch, rho0=1.0):
-    """k_g of a uniform periodic medium after nsteps steps from rest.
-    Written directly from Eq. 2, 16a-b, 17 (rho stays rho0; the momentum of
-    a node gains rho F per step); accepts complex log_k / eps."""
+def uniform_velocity(log_k, eps, nsteps, G, forch, rho0=1.0):
+    """Velocity (u_x, u_y) of a uniform periodic medium after nsteps steps
+    from rest.  Written directly from Eq. 2, 16a-b, 17 (rho stays rho0; the
+    momentum of a node gains rho F per step); accepts complex log_k / eps."""
     k = np.exp(log_k)
     G = np.asarray(G, dtype=float)
     m = np.zeros(2, dtype=complex)
@@ -48,7 +48,13 @@ def uniform_kg(log_k, eps, nsteps, G, forch, rho0=1.0):
                 u[0] * u[0] + u[1] * u[1])
         F = eps * G - drag * u
         m = m + rho0 * F
-    return NU * velocity(m)[0] / G[0]
+    return velocity(m)
+
+
+def uniform_kg(log_k, eps, nsteps, G, forch, rho0=1.0):
+    """k_g of a uniform periodic medium after nsteps steps from rest (the
+    mean velocity is the velocity of every node)."""
+    return NU * uniform_velocity(log_k, eps, nsteps, G, forch, rho0)[0] / G[0]
 
 
 def complex_step(f, x, h=1e-30):

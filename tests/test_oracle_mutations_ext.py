@@ -1,7 +1,7 @@
 """Planted mistakes in the oracle's physical inputs (Eq. 9-11), first-order
-factor (Eq. 4-5), dynamic Knudsen number, velocity histogram (Fig. 6) and
-central-difference gradient: each must be caught by the pins written for
-that function (no GPU).  The planted copies are compiled to a temporary
+factor (Eq. 4-5), dynamic Knudsen number, velocity histogram (Fig. 6),
+central-difference gradient, steady-state residual and mass: each must be
+caught by the pins written for that function (no GPU).  The planted copies are compiled to a temporary
 directory; the oracle itself is never modified."""
 import os
 import subprocess
@@ -11,6 +11,7 @@ import pytest
 import test_oracle_gradient as grad
 import test_oracle_histogram as hist
 import test_oracle_physical as phys
+import test_oracle_reductions as red
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "oracle", "lbm_oracle.c")
@@ -26,6 +27,8 @@ HIST = [hist.test_uniform_flow_fills_last_bin, hist.test_no_flow_fills_first_bin
         hist.test_channel_histogram_follows_eq20, hist.test_layered_darcy_flow_bins]
 GRAD = [lambda: grad.test_uniform_sum_matches_scalar_recurrence(0),
         lambda: grad.test_uniform_sum_matches_scalar_recurrence(1), grad.test_node_indexing]
+RES = red.RESIDUAL_PINS
+MASS = red.MASS_PINS
 
 # (name, exact text in the oracle, planted replacement, pins that must catch it)
 MUTATIONS = [
@@ -55,6 +58,23 @@ MUTATIONS = [
     ("fd_linear_in_k", "pk[j] = k_i[j] * exp(sign * h);", "pk[j] = k_i[j] + sign * h;", GRAD),
     ("fd_wrong_node", "const int64_t j = nodes[e / 2];", "const int64_t j = nodes[e / 2] + 1;",
      GRAD),
+    ("residual_no_sqrt", "return sqrt(num) / sqrt(den);", "return num / den;", RES),
+    ("residual_norm_of_snapshot", "den += u[0] * u[0] + u[1] * u[1];",
+     "den += ux_prev[j] * ux_prev[j] + uy_prev[j] * uy_prev[j];", RES),
+    ("residual_drops_y", "num += dx * dx + dy * dy;", "num += dx * dx;", RES),
+    ("residual_over_plate_rows",
+     "double num = 0.0, den = 0.0;\n  for (int y = 0; y < p->ny; ++y) {\n"
+     "    if (orc_is_wall_row(p, y)) continue;",
+     "double num = 0.0, den = 0.0;\n  for (int y = 0; y < p->ny; ++y) {\n", RES),
+    ("residual_skips_last_column", "  double num = 0.0, den = 0.0;\n  for (int y = 0; y < p->ny; ++y) {\n"
+     "    if (orc_is_wall_row(p, y)) continue;\n    for (int x = 0; x < p->nx; ++x) {",
+     "  double num = 0.0, den = 0.0;\n  for (int y = 0; y < p->ny; ++y) {\n"
+     "    if (orc_is_wall_row(p, y)) continue;\n    for (int x = 0; x < p->nx - 1; ++x) {", RES),
+    ("mass_over_plate_rows",
+     "double m = 0.0;\n  for (int y = 0; y < p->ny; ++y) {\n    if (orc_is_wall_row(p, y)) continue;",
+     "double m = 0.0;\n  for (int y = 0; y < p->ny; ++y) {\n", MASS),
+    ("mass_drops_rest_population", "for (int i = 0; i < 9; ++i) m += s->f[j * 9 + i];",
+     "for (int i = 1; i < 9; ++i) m += s->f[j * 9 + i];", MASS),
 ]
 
 
