@@ -10,14 +10,21 @@ the FP16-stored run is reported beside it.
 
 One JSON line on rank 0:
   value     lattice updates per second (GLUPS) of ``lbmp_step`` with the
-            lattice resident in HBM (1.3 GB FP32 working set >> 129 MB L2)
+            lattice resident in HBM (1.3 GB FP32 working set >> 129 MB L2);
+            the median of five timed regions of K steps
   e2e       the same metric through the public API from host buffers:
             lbmp_set_fields from host arrays + K steps + lbmp_permeability
   roofline  the fused step kernel against the measured HBM copy bandwidth
-  cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample
+            (and the data-sheet figure)
+  cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample,
+            and on one core
+  k_g_vs_oracle  k_g of FP32 and FP16 storage against the oracle's, on the
+            oracle's own run (a crop of the workload from rest)
   adjoint   one gradient of k_g (lbmp_permeability_gradient) over 20000
             steps of the 1024^2 two-component medium, with its backward
             sweep against the HBM roofline
+  batch     a subset of the batched sweep (two-component media of uneven
+            sizes x Knudsen numbers), FP16 and FP32, tuned launch shape
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
 With torchrun and N > 1 ranks every rank runs an independent replica (the
@@ -39,6 +46,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D2Q9 porous-LBM GLUPS & %HBM peak, FP32 vs FP16-stored at <=1e-3 k_a err"
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0   # HBM3e of a GB300, the data-sheet figure
 
 
 def parse():
@@ -69,6 +77,12 @@ def parse():
                     help="skip the dynamic-Kn object of the default line")
     ap.add_argument("--batch-media", type=int, default=256)
     ap.add_argument("--batch-kn", type=int, default=8)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-sweep object of the default line")
+    ap.add_argument("--batch-object-media", type=int, default=32,
+                    help="media of the default line's batched-sweep object (x --batch-kn "
+                         "Knudsen numbers)")
+    ap.add_argument("--batch-object-steps", type=int, default=300)
     ap.add_argument("--kernel", choices=["auto", "staged", "direct"], default="auto",
                     help="implementation of the step kernel (auto: direct for FP32 storage, "
                          "staged for FP16)")
@@ -177,25 +191,52 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU (oracle)
-def oracle_rate(med, cfg, seconds: float, crop: int = 1024):
-    """FP64 oracle lattice updates per second on a crop of the workload."""
+def oracle_rate(med, cfg, seconds: float, crop: int = 1024, threads: int = 0):
+    """FP64 oracle lattice updates per second on a crop of the workload, on
+    all host cores (threads = 0) or on `threads` of them.  Also returns the
+    oracle's k_g at the end of the run and the steps taken from rest."""
     from oracle import oracle
     n = min(crop, cfg["nx"])
     sub = med.crop(n, n)
     p = oracle.make_params(n, n, tau=cfg["tau"], bc_x=cfg["bc_x"], bc_y=cfg["bc_y"],
                            rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
                            forchheimer=cfg["forchheimer"])
-    sim = oracle.OracleSim(p)
-    sim.set_fields(sub.eps, sub.k_i, sub.kn)
-    sim.step(1)
-    t0 = time.perf_counter()
-    sim.step(1)
-    per = time.perf_counter() - t0
-    steps = max(2, int(seconds / max(per, 1e-6)))
-    t0 = time.perf_counter()
-    sim.step(steps)
-    dt = time.perf_counter() - t0
-    return n * n * steps / dt, steps, n, oracle.max_threads()
+    all_cores = oracle.max_threads()
+    used = threads if threads > 0 else all_cores
+    oracle.set_threads(used)
+    try:
+        sim = oracle.OracleSim(p)
+        sim.set_fields(sub.eps, sub.k_i, sub.kn)
+        sim.step(1)
+        t0 = time.perf_counter()
+        sim.step(1)
+        per = time.perf_counter() - t0
+        steps = max(2, int(seconds / max(per, 1e-6)))
+        t0 = time.perf_counter()
+        sim.step(steps)
+        dt = time.perf_counter() - t0
+        kg, _ = sim.permeability()
+    finally:
+        oracle.set_threads(all_cores)
+    return dict(rate=n * n * steps / dt, steps=steps, n=n, cores=used, k_g=kg,
+                total_steps=steps + 2)
+
+
+def gpu_crop_kg(lbmp, med, cfg, n: int, steps: int, storage: str, rounding: str) -> float:
+    """k_g of the GPU path (AUTO kernel) on the n x n crop after `steps`
+    steps from rest, for the comparison with the oracle's run."""
+    sub = med.crop(n, n)
+    sc = lbmp.SimConfig(n, n, tau=cfg["tau"], bc_x=cfg["bc_x"], bc_y=cfg["bc_y"],
+                        rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
+                        forchheimer=cfg["forchheimer"],
+                        storage=lbmp.STORE_FP32 if storage == "fp32" else lbmp.STORE_FP16,
+                        fp16_rounding=(lbmp.ROUND_STOCHASTIC if rounding == "stochastic"
+                                       else lbmp.ROUND_NEAREST))
+    with lbmp.Sim(sc) as sim:
+        sim.set_fields(sub.eps, sub.k_i, sub.kn)
+        sim.step(steps)
+        kg, _ = sim.permeability()
+    return kg
 
 
 def run_reference(args, ws, rank):
@@ -245,8 +286,11 @@ def kn_beta_for(cfg, p_ratio: float = 2.0) -> float:
     return (p_ratio - 1.0) / (a - p_ratio * b)
 
 
+REPEATS = 5   # timed K-step regions per measurement; the median is reported
+
+
 def time_storage(lbmp, torch, med, cfg, storage, K, W, kernel, rounding="stochastic",
-                 kn_beta=0.0):
+                 kn_beta=0.0, repeats=REPEATS):
     st = lbmp.STORE_FP32 if storage == "fp32" else lbmp.STORE_FP16
     sc = lbmp.SimConfig(cfg["nx"], cfg["ny"], tau=cfg["tau"], bc_x=cfg["bc_x"],
                         bc_y=cfg["bc_y"], rho_in=cfg["rho_in"], rho_out=cfg["rho_out"],
@@ -258,21 +302,25 @@ def time_storage(lbmp, torch, med, cfg, storage, K, W, kernel, rounding="stochas
     sim = lbmp.Sim(sc)
     sim.set_fields(med.eps, med.k_i, med.kn)
     sim.step(W)
+    sim.step(K)   # untimed: builds the step graphs a K-step call replays
     sim.synchronize()
     info0 = sim.info()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    if torch.distributed.is_initialized():
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    e0.record(sim.stream)
-    sim.step(K)
-    e1.record(sim.stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    samples = []
+    for _ in range(repeats):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(sim.stream)
+        sim.step(K)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        samples.append(e0.elapsed_time(e1))
+    ms = statistics.median(samples)
     info1 = sim.info()
     kg, um = sim.permeability()
-    out = dict(ms=ms, launches=int(info1.launches - info0.launches),
+    out = dict(ms=ms, ms_samples=samples, launches=int(info1.launches - info0.launches) // repeats,
                nodes=int(info1.fluid_nodes), bpu=float(info1.bytes_per_update),
                scale=float(info1.fp16_scale), k_g=kg)
     sim.close()
@@ -285,9 +333,9 @@ def time_e2e(lbmp, torch, med, cfg, K):
                         forchheimer=cfg["forchheimer"], storage=lbmp.STORE_FP32)
     sim = lbmp.Sim(sc)
     import numpy as np
-    eps = np.ascontiguousarray(med.eps)
-    k_i = np.ascontiguousarray(med.k_i)
-    kn = np.ascontiguousarray(med.kn)
+    # the inputs sit in pinned host memory, as a serving process keeps them
+    eps, k_i, kn = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                    for a in (med.eps, med.k_i, med.kn))
     sim.set_fields(eps, k_i, kn)  # warm the allocator and the graphs
     sim.step(64)
     sim.permeability()
@@ -352,6 +400,7 @@ def run_ours(args, ws, rank, local):
         dyn = time_storage(lbmp, torch, med, cfg, "fp32", K, W, "auto",
                            kn_beta=kn_beta_for(cfg))
     adj = None if args.no_adjoint else adjoint_time(lbmp, torch, args.adjoint_steps)
+    batch = None if args.no_batch else batch_object(lbmp, torch, args)
 
     # slowest rank decides
     ms = reduce_max(res["ms"], "cuda")
@@ -374,9 +423,11 @@ def run_ours(args, ws, rank, local):
         tr = profiled_traffic(tag, src)
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "bytes_per_update": r["bpu"],
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
                 "traffic_per_update": (tr["dram_bytes_per_launch"] / r["nodes"] if tr else None),
+                "achieved_dram": (tr["dram_bytes_per_launch"] / per_launch_s / 1e9 if tr else None),
                 "kernel": kernel_name(args.kernel, tag)}
 
     line = {
@@ -384,7 +435,9 @@ def run_ours(args, ws, rank, local):
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**config_dict(args, cfg, primary), "kernel": args.kernel,
-                   "fp16_rounding": args.fp16_rounding},
+                   "fp16_rounding": args.fp16_rounding,
+                   "timing": f"median of {REPEATS} timed regions of K steps, CUDA events"},
+        "ms_per_step_samples": [t / K for t in res["ms_samples"]],
         "roofline": roofline(res, "StoreF32" if primary == "fp32" else "StoreF16"),
         "gpu_launches": res["launches"],
         "clocks": clocks,
@@ -394,6 +447,7 @@ def run_ours(args, ws, rank, local):
         g2 = ws * res_other["nodes"] * K / (res_other["ms"] * 1e-3) / 1e9
         line[f"{other}_stored"] = {
             "value": g2, "unit": "GLUPS", "ms_per_step": res_other["ms"] / K,
+            "ms_per_step_samples": [t / K for t in res_other["ms_samples"]],
             "ratio_fp16_over_fp32": (g2 / glups) if other == "fp16" else (glups / g2),
             "roofline": roofline(res_other, "StoreF32" if other == "fp32" else "StoreF16"),
             "fp16_scale": res_other["scale"], "k_g": res_other["k_g"],
@@ -401,7 +455,7 @@ def run_ours(args, ws, rank, local):
     if e2e:
         line["e2e"] = {"value": ws * nodes * K / e2e["s"] / 1e9, "unit": "GLUPS",
                        "h2d_bytes_per_step": e2e["h2d"] / K, "d2h_bytes_per_step": e2e["d2h"] / K,
-                       "what": "lbmp_set_fields from host float64 arrays + K steps + "
+                       "what": "lbmp_set_fields from pinned host float64 arrays + K steps + "
                                "lbmp_permeability to host, wall clock"}
     if dyn:
         g3 = ws * dyn["nodes"] * K / (dyn["ms"] * 1e-3) / 1e9
@@ -417,18 +471,41 @@ def run_ours(args, ws, rank, local):
             "ratio_to_static": g3 / glups, "roofline": r, "k_g": dyn["k_g"]}
     if adj:
         line["adjoint"] = adjoint_object(adj, peak, peak_kind)
+    if batch:
+        line["batch"] = batch
     if not args.no_cpu and ws == 1:
-        rate, steps, n, cores = oracle_rate(med, cfg, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "GLUPS", "cores": cores,
-                                "kind": "oracle",
-                                "sample": f"{n}x{n} crop of the workload, {steps} FP64 steps"}
+        o = oracle_rate(med, cfg, args.cpu_seconds)
+        o1 = oracle_rate(med, cfg, args.cpu_seconds / 3, crop=256, threads=1)
+        line["cpu_baseline"] = {
+            "value": o["rate"] / 1e9, "unit": "GLUPS", "cores": o["cores"], "kind": "oracle",
+            "sample": f"{o['n']}x{o['n']} crop of the workload, {o['steps']} FP64 steps",
+            "single_thread": {"value": o1["rate"] / 1e9, "unit": "GLUPS", "cores": 1,
+                              "sample": f"{o1['n']}x{o1['n']} crop of the workload, "
+                                        f"{o1['steps']} FP64 steps"}}
+        # each storage against the oracle's k_g on the oracle's own run: the
+        # crop, from rest, the same number of steps
+        n, S = o["n"], o["total_steps"]
+        errs = {"sample": f"{n}x{n} crop of the workload, {S} steps from rest",
+                "k_g_oracle": o["k_g"]}
+        for st in ("fp32", "fp16"):
+            kg = gpu_crop_kg(lbmp, med, cfg, n, S, st, args.fp16_rounding)
+            errs[st] = {"k_g": kg, "rel_err": abs(kg / o["k_g"] - 1.0)}
+        line["k_g_vs_oracle"] = errs
+        line["k_g_err_vs_oracle"] = errs[primary]["rel_err"]
+        if res_other:
+            line[f"{other}_stored"]["k_g_err_vs_oracle"] = errs[other]["rel_err"]
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
 # ------------------------------------------------------------------ adjoint
-ADJOINT_BYTES_PER_NODE = 36 + 36 + 8 + 16 + 36 + 48 / 32  # see adjoint_time()
+# algorithmic bytes per node and time step of the backward sweep (see
+# adjoint_time()): the recompute step (the forward step's 80 plus 12 of
+# moments) and the reverse step (109.5)
+ADJOINT_RECOMPUTE_BYTES = 80 + 12
+ADJOINT_REVERSE_BYTES = 36 + 12 + 8 + 16 + 36 + 48 / 32
+ADJOINT_BYTES_PER_NODE = ADJOINT_RECOMPUTE_BYTES + ADJOINT_REVERSE_BYTES
 
 
 def adjoint_case(lbmp, n: int = 1024):
@@ -444,10 +521,11 @@ def adjoint_case(lbmp, n: int = 1024):
 
 def adjoint_time(lbmp, torch, N: int, evals: int = 1, warm: int = 1, n: int = 1024):
     """Times lbmp_permeability_gradient (N steps from rest) with CUDA events
-    on the library's stream, and the plain N-step run beside it.  The
-    backward sweep is the gradient time minus the forward and the recompute
-    passes (two timed forward runs).  Algorithmic bytes of one reverse step
-    per node: mu^{t+1} gathered 36, f^t pulled 36, medium 8, FP32
+    on the library's stream (median of `evals`), and the plain N-step run
+    beside it.  The backward sweep is the gradient time minus the forward
+    pass (one timed forward run): per node and time step it recomputes the
+    forward step, storing the moments (80 + 12 bytes), and runs the reverse
+    step: mu^{t+1} gathered 36, moments of f^t 12, medium 8, FP32
     accumulators read + written 16, mu^t written 36, plus the FP64 fold
     (8 + 32 + 8 bytes every 32 steps)."""
     import math
@@ -477,16 +555,17 @@ def adjoint_time(lbmp, torch, N: int, evals: int = 1, warm: int = 1, n: int = 10
         t_grad.append(e0.elapsed_time(e1))
     launches = (sim.info().launches - l0) // evals
     nodes = int(sim.info().fluid_nodes)
+    pitch = int(sim.info().pitch)
     sim.close()
     every = math.ceil(math.sqrt(N))
     nseg = math.ceil(N / every)
-    state = 9 * 4 * (((n + 63) // 64) * 64) * n
-    tg = min(t_grad)
-    t_back = tg - 2.0 * t_fwd
+    state = 9 * 4 * pitch * n
+    tg = statistics.median(t_grad)
+    t_back = tg - t_fwd
     return dict(ms_gradient=tg, ms_forward=t_fwd, ms_backward=t_back, nodes=nodes, N=N,
                 every=every, checkpoints=nseg, launches=int(launches), k_g=kg,
                 sum_abs_dlogk=float(gl.abs().sum()), sum_abs_deps=float(ge.abs().sum()),
-                device_bytes=(nseg + every + 3) * state + 24 * state // 36)
+                device_bytes=(nseg + 4) * state + every * state // 3 + 24 * state // 36)
 
 
 def adjoint_object(r, peak, peak_kind):
@@ -508,8 +587,10 @@ def adjoint_object(r, peak, peak_kind):
                      "bytes_per_update": ADJOINT_BYTES_PER_NODE,
                      "traffic": (tr["dram_bytes_per_launch"] if tr else None),
                      "traffic_per_update": (tr["dram_bytes_per_launch"] / tr["nodes"] if tr else None),
-                     "kernel": "lbmp::adjoint_step_kernel<false> (+ fold)",
-                     "timing": "gradient minus forward and recompute passes, CUDA events"},
+                     "kernel": "lbmp::step_kernel<StoreF32, 0, 0, 1> (recompute with moments) + "
+                               "lbmp::adjoint_step_kernel<false> (+ fold)",
+                     "timing": "backward sweep (recompute + reverse) = gradient minus the "
+                               "forward pass, CUDA events"},
         "k_g": r["k_g"],
     }
 
@@ -558,23 +639,20 @@ def batch_media(n_media: int, seed0: int = 1000):
     return [media.two_component(int(n), seed=seed0 + m, corr_len=32.0) for m, n in enumerate(sides)]
 
 
-def run_batch(args, ws, rank, local):
-    """One persistent launch per step over every (medium, Kn) instance."""
+def batch_measure(lbmp, torch, n_media: int, n_kn: int, storage: str, K: int, W: int,
+                  rounding: str = "stochastic", repeats: int = REPEATS, clocks_index=None):
+    """Builds the batched sweep (n_media media x n_kn Knudsen numbers), tunes
+    its launch shape, and times K steps `repeats` times (median) with CUDA
+    events on the batch's stream."""
     import numpy as np
-    import torch
-    from paper_1411_7051_gb300 import lbmp
-    torch.cuda.set_device(local)
-    if ws > 1:
-        torch.distributed.init_process_group("nccl")
-    K, W = args.steps, max(3, args.warmup)
     t0 = time.perf_counter()
-    meds = batch_media(args.batch_media)
-    kns = np.logspace(-3, 1, args.batch_kn)
+    meds = batch_media(n_media)
+    kns = np.logspace(-3, 1, n_kn)
     sizes = [(m.eps.shape[1], m.eps.shape[0]) for m in meds for _ in kns]
-    storage = lbmp.STORE_FP32 if args.storage == "fp32" else lbmp.STORE_FP16
+    st = lbmp.STORE_FP32 if storage == "fp32" else lbmp.STORE_FP16
     cfg = lbmp.SimConfig(1, 1, tau=0.8, bc_x=lbmp.BCX_PRESSURE, bc_y=lbmp.BCY_WALLS,
-                         rho_in=1.0005, rho_out=0.9995, forchheimer=1, storage=storage,
-                         fp16_rounding=(lbmp.ROUND_STOCHASTIC if args.fp16_rounding == "stochastic"
+                         rho_in=1.0005, rho_out=0.9995, forchheimer=1, storage=st,
+                         fp16_rounding=(lbmp.ROUND_STOCHASTIC if rounding == "stochastic"
                                         else lbmp.ROUND_NEAREST))
     b = lbmp.Batch(cfg, sizes)
     j = 0
@@ -586,25 +664,84 @@ def run_batch(args, ws, rank, local):
     chosen, tune_ms = b.tune(steps=5)
     b.step(W)
     b.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        l0 = b.info().launches
+    samples = []
+    clk = ClockSampler(clocks_index) if clocks_index is not None else None
+    if clk:
+        clk.__enter__()
+    l0 = b.info().launches
+    for _ in range(repeats):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
         e0.record(b.stream)
         b.step(K)
         e1.record(b.stream)
         torch.cuda.synchronize()
-    ms = reduce_max(e0.elapsed_time(e1), "cuda")
+        samples.append(e0.elapsed_time(e1))
+    if clk:
+        clk.__exit__(None, None, None)
     info = b.info()
     kg, _ = b.permeability()
+    b.close()
+    return dict(ms=statistics.median(samples), ms_samples=samples, nodes=int(info.total_nodes),
+                instances=len(sizes), bpu=float(info.bytes_per_update),
+                shape=[info.shape_threads, info.shape_nodes_per_thread,
+                       {0: "one block per item", 1: "persistent",
+                        2: "staged (bulk-copy tiles)"}[int(info.persistent)]],
+                staged=int(info.persistent) == 2, launches=int(info.launches - l0) // repeats,
+                setup_s=setup_s, chosen=chosen, tune_ms=tune_ms,
+                k_g_range=[float(np.min(kg)), float(np.max(kg))],
+                clocks=clk.summary() if clk else None)
+
+
+def batch_roofline(r, K, peak, kind):
+    achieved = r["bpu"] * r["nodes"] / (r["ms"] * 1e-3 / K) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": f"of {kind}",
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
+            "bytes_per_update": r["bpu"], "traffic": None,
+            "kernel": ("lbmp::batch_staged_kernel" if r["staged"] else "lbmp::batch_step_kernel")}
+
+
+def batch_object(lbmp, torch, args):
+    """The default line's batched-sweep object: a subset of the sweep (the
+    first --batch-object-media media x --batch-kn Knudsen numbers), FP16
+    (stochastic rounding) and FP32 storage."""
+    peak, kind = measured_peaks()
+    K, W = args.batch_object_steps, 10
+    out = {"workload": f"batched sweep subset: {args.batch_object_media} two-component media "
+                       f"(sides {list(BATCH_SIDES)}, corr. length 32) x {args.batch_kn} Kn in "
+                       "[1e-3, 10], pressure x, walls y, Forchheimer on; one launch per step "
+                       f"over all instances; median of {REPEATS} regions of {K} steps",
+           "steps": K}
+    for st in ("fp16", "fp32"):
+        r = batch_measure(lbmp, torch, args.batch_object_media, args.batch_kn, st, K, W,
+                          args.fp16_rounding)
+        out[st] = {"value": r["nodes"] * K / (r["ms"] * 1e-3) / 1e9, "unit": "GLUPS",
+                   "ms_per_step": r["ms"] / K, "instances": r["instances"], "nodes": r["nodes"],
+                   "shape": r["shape"], "tuned_shape_index": r["chosen"],
+                   "roofline": batch_roofline(r, K, peak, kind), "gpu_launches": r["launches"],
+                   "k_g_range": r["k_g_range"], "setup_s": r["setup_s"]}
+    return out
+
+
+def run_batch(args, ws, rank, local):
+    """One persistent launch per step over every (medium, Kn) instance."""
+    import torch
+    from paper_1411_7051_gb300 import lbmp
+    torch.cuda.set_device(local)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl")
+    K, W = args.steps, max(3, args.warmup)
+    storage = args.storage or "fp16"
+    r = batch_measure(lbmp, torch, args.batch_media, args.batch_kn, storage, K, W,
+                      args.fp16_rounding, clocks_index=local)
+    ms = reduce_max(r["ms"], "cuda")
     if rank == 0:
-        nodes = int(info.total_nodes)
-        glups = whole_job_glups(ws, nodes, K, ms)
+        glups = whole_job_glups(ws, r["nodes"], K, ms)
         peak, kind = measured_peaks()
-        achieved = info.bytes_per_update * nodes / (ms * 1e-3 / K) / 1e9
         line = {
             "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": K,
             "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -612,23 +749,16 @@ def run_batch(args, ws, rank, local):
             "config": {"workload": f"batched sweep: {args.batch_media} two-component media "
                                    f"(sides {list(BATCH_SIDES)}) x {args.batch_kn} Kn in [1e-3, 10], "
                                    "pressure x, walls y, Forchheimer on, one persistent launch per step",
-                       "instances": len(sizes), "nodes": nodes,
-                       "storage": "fp16" if storage == lbmp.STORE_FP16 else "fp32",
-                       "shape": [info.shape_threads, info.shape_nodes_per_thread,
-                                 {0: "one block per item", 1: "persistent",
-                                  2: "staged (bulk-copy tiles)"}[int(info.persistent)]],
-                       "l2": "inputs larger than L2, no flush"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": f"of {kind}",
-                         "bytes_per_update": info.bytes_per_update, "traffic": None,
-                         "kernel": ("lbmp::batch_staged_kernel" if int(info.persistent) == 2
-                                    else "lbmp::batch_step_kernel")},
-            "gpu_launches": int(info.launches - l0), "clocks": clk.summary(),
-            "setup_s": setup_s, "tuned_shape_index": chosen, "tune_ms_per_step": tune_ms,
-            "k_g_range": [float(np.min(kg)), float(np.max(kg))],
+                       "instances": r["instances"], "nodes": r["nodes"], "storage": storage,
+                       "shape": r["shape"], "l2": "inputs larger than L2, no flush",
+                       "timing": f"median of {REPEATS} timed regions of K steps, CUDA events"},
+            "ms_per_step_samples": [t / K for t in r["ms_samples"]],
+            "roofline": batch_roofline(r, K, peak, kind),
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "setup_s": r["setup_s"], "tuned_shape_index": r["chosen"],
+            "tune_ms_per_step": r["tune_ms"], "k_g_range": r["k_g_range"],
         }
         print(json.dumps(line), flush=True)
-    b.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 

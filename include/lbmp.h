@@ -160,6 +160,15 @@ lbmp_status lbmp_synchronize(lbmp_ctx *ctx);
 lbmp_status lbmp_macroscopic(lbmp_ctx *ctx, double *rho, double *ux, double *uy,
                              int32_t where);
 
+/* Apparent permeability k_a = k_i f_c(Kn) (Eq. 3 with Eq. 6-7, or Eq. 4-5)
+ * of every node as the step uses it: the reciprocal of the FP32 1/k_a that
+ * lbmp_set_fields stored (f_c evaluated in FP32), [ny][nx] float64; +inf
+ * for an open pore, whatever the porosity of the node.  With a dynamic Kn,
+ * k_a at the reference pressure p0 (the step's FP32 f_c of the Kn given).
+ * Plate rows read 0.  Synchronous.  Errors: EINVAL, ESTATE (no fields
+ * set), ECUDA. */
+lbmp_status lbmp_apparent_permeability(lbmp_ctx *ctx, double *ka, int32_t where);
+
 /* Post-stream populations f_i(x, t) of the current time level,
  * [9][ny][nx] float64; wall rows read 0.  Synchronous. */
 lbmp_status lbmp_populations(lbmp_ctx *ctx, double *f, int32_t where);
@@ -262,8 +271,10 @@ lbmp_status lbmp_get_info(lbmp_ctx *ctx, lbmp_info *out);
  * nodes the derivatives of the flow part are the one-sided ones of the
  * branch the step takes there (0 for d_logk).  The forward states are
  * recomputed from checkpoints taken every `every` steps (0: ceil(sqrt(
- * nsteps))), holding ceil(nsteps / every) + every + 3 population buffers on
- * the device (FP32, like the adjoint populations); each reverse step's
+ * nsteps))), of which the reverse steps need only the moments (rho, m):
+ * the device holds ceil(nsteps / every) + 4 population buffers (FP32, like
+ * the adjoint populations) and the moments of `every` levels (a third of a
+ * population buffer each); each reverse step's
  * parameter derivatives are summed in FP32 over at most 32 steps, then in
  * FP64.  The context is left at time level nsteps of a run from rest (its
  * previous state is replaced).  Needs FP32 storage.  Synchronous.

@@ -42,7 +42,8 @@ struct AdjArgs {
   StepArgs a;            // forward parameters (FP32 storage, scale 1)
   const float *lam_in;   // mu^{t+1}, [9][ny][pitch] (pressure columns unused)
   float *lam_out;        // mu^t
-  const float *fin;      // forward buffer whose pull gives f^t
+  const float *fin;      // forward buffer whose pull gives f^t (seed step)
+  const float *mom;      // moments of f^t (rho - rho0, m_x, m_y planes; reverse steps)
   const float2 *med;     // (eps, 1/k_a)
   float2 *acc;           // [ny][pitch] (dJ/d eps, dJ/d ln k_a) of the last few steps, FP32
   double *g_eps;         // [ny][pitch] dJ/d eps, FP64 (acc folded in every kFold steps)
@@ -291,10 +292,16 @@ __device__ __forceinline__ void column_adjoint(const AdjArgs &A, int x, int y, f
     const int xb = side ? a.nx - 1 : 0;
     const long long jb = (long long)y * a.pitch + xb;
     const float2 mb = A.med[jb];
-    float fb[9];
-    pressure_node<StoreF32>(A.fin, A.med, a, xb, y, mb.x, fb);
     float rb, mbx, mby;
-    moments(fb, a.rho0, rb, mbx, mby);
+    if (SEED) {
+      float fb[9];
+      pressure_node<StoreF32>(A.fin, A.med, a, xb, y, mb.x, fb);
+      moments(fb, a.rho0, rb, mbx, mby);
+    } else {  // the column's moments as its forward step stored them
+      rb = a.rho0 + A.mom[jb];
+      mbx = A.mom[a.plane + jb];
+      mby = A.mom[2 * a.plane + jb];
+    }
     Bar bb = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     float lb[9];
     if (SEED) {
@@ -339,10 +346,18 @@ __global__ void __launch_bounds__(kAdjBX, 8) adjoint_step_kernel(const AdjArgs A
   // population loads
   const float2 g0 = A.acc[j];
   const float2 m = __ldg(A.med + j);
-  float d[9], mu[9];
-  pull_node<StoreF32>(A.fin, a, x, y, d);
+  float mu[9];
   float rho, mx, my;
-  moments(d, a.rho0, rho, mx, my);
+  if (SEED) {
+    float d[9];
+    pull_node<StoreF32>(A.fin, a, x, y, d);
+    moments(d, a.rho0, rho, mx, my);
+  } else {  // the moments of f^t, stored by the recompute step (bit for bit
+            // the sums above)
+    rho = a.rho0 + A.mom[j];
+    mx = A.mom[a.plane + j];
+    my = A.mom[2 * a.plane + j];
+  }
   Bar b = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   if (SEED) {
     if (m.x > 0.0f) {
@@ -467,17 +482,20 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
     const size_t state = c->buf_bytes();
     const size_t field = (size_t)c->plane * sizeof(double);
     cudaStream_t s = c->stream;
-    // checkpoints (one per segment), the states of one segment, the two
-    // adjoint levels, the FP64 gradient fields
-    DevBuf ck, seg, lam, grad, outs;
+    // checkpoints (one per segment), two states for the recompute, the
+    // moments of the levels of one segment, the two adjoint levels, the FP64
+    // gradient fields
+    const size_t mom_level = (size_t)c->plane * 3 * sizeof(float);
+    DevBuf ck, seg, mom, lam, grad, outs;
     ACK(cudaMalloc(&ck.p, state * (size_t)nseg));
-    ACK(cudaMalloc(&seg.p, state * (size_t)(every + 1)));
+    ACK(cudaMalloc(&seg.p, state * 2));
+    ACK(cudaMalloc(&mom.p, mom_level * (size_t)every));
     ACK(cudaMalloc(&lam.p, state * 2));
     const size_t accb = (size_t)c->plane * sizeof(float2);
     ACK(cudaMalloc(&grad.p, field * 2 + accb));
     ACK(cudaMemsetAsync(lam.p, 0, state * 2, s));
     ACK(cudaMemsetAsync(grad.p, 0, field * 2 + accb, s));
-    char *ckp = (char *)ck.p, *segp = (char *)seg.p;
+    char *ckp = (char *)ck.p, *segp = (char *)seg.p, *momp = (char *)mom.p;
     float *lam0 = (float *)lam.p, *lam1 = (float *)((char *)lam.p + state);
     double *g_eps = (double *)grad.p, *g_lk = (double *)((char *)grad.p + field);
     float2 *acc = (float2 *)((char *)grad.p + 2 * field);
@@ -521,23 +539,28 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
     // seed: Lambda^N = dJ/df^N
     const dim3 blk(lbmp::kAdjBX), grd((a.nx + lbmp::kAdjBX - 1) / lbmp::kAdjBX, rows);
     A.fin = (const float *)c->buf[cur];
+    A.mom = nullptr;
     A.lam_in = lam1;
     A.lam_out = lam0;
     lbmp::adjoint_step_kernel<true><<<grd, blk, 0, s>>>(A);
     ACK(cudaGetLastError());
     // backward, one segment at a time: recompute its levels from the
-    // checkpoint, then run the reverse steps over them
+    // checkpoint (keeping only their moments), then run the reverse steps
+    // over them
     float *lam_next = lam0, *lam_prev = lam1;  // Lambda^{t+1}, Lambda^t
     int64_t reversed = 0;  // the FP32 accumulators fold every kFold reverse steps
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
       const int64_t t0 = sg * every, n = std::min(every, nsteps - t0);
       ACK(cudaMemcpyAsync(segp, ckp + state * sg, state, cudaMemcpyDeviceToDevice, s));
       for (int64_t t = 0; t < n; ++t)
-        ACK(forward_step(c, a, segp + state * t, segp + state * (t + 1), s));
+        ACK(lbmp::launch_step_moments(a, rows, (const float *)(segp + state * (t & 1)),
+                                      (float *)(segp + state * ((t + 1) & 1)), c->med,
+                                      (float *)(momp + mom_level * t), s));
       for (int64_t t = n - 1; t >= 0; --t) {
         A.lam_in = lam_next;
         A.lam_out = lam_prev;
-        A.fin = (const float *)(segp + state * t);
+        A.fin = nullptr;
+        A.mom = (const float *)(momp + mom_level * t);
         lbmp::adjoint_step_kernel<false><<<grd, blk, 0, s>>>(A);
         ACK(cudaGetLastError());
         std::swap(lam_next, lam_prev);

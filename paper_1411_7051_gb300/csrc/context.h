@@ -48,7 +48,8 @@ struct lbmp_ctx {
   int alloc_count = 0;
   int fault_alloc_at = 0;       // simulated allocation failure (testing)
   int drop_tile = -1;           // withheld tile of the staged kernel (testing)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // step graphs: [l][cur] replays 2^l steps starting from buffer cur
+  cudaGraphExec_t graph[6][2] = {};
 
   lbmp::StepArgs args() const {
     lbmp::StepArgs a;

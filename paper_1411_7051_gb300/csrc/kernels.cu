@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "kernels.h"
 #include "lattice.cuh"
 #include "staged.cuh"
@@ -32,11 +34,15 @@ constexpr int kMediumBX = 256;
 // bump_kernel after a group of launches).
 // DYN: Knudsen number per node and step from the local pressure (the
 // medium holds 1/k_i, a.kn0 the Kn at p0).
-template <class S, bool SR, bool DYN>
+// MOM: also store each node's post-stream moments (rho - rho0, m_x, m_y;
+// three [ny][pitch] planes at mom, a.plane apart) -- all that the reverse
+// step of the adjoint needs of the forward state.
+template <class S, bool SR, bool DYN, bool MOM = false>
 __global__ void __launch_bounds__(kStepBX)
     step_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
                 typename S::T *__restrict__ fout, const float2 *__restrict__ med,
-                const unsigned long long *__restrict__ tctr, int k) {
+                const unsigned long long *__restrict__ tctr, int k,
+                float *__restrict__ mom) {
   const int y = a.y0 + blockIdx.y;
   const int xb = blockIdx.x * (kStepBX * kStepNPT) + threadIdx.x;
   const long long row = (long long)y * a.pitch;
@@ -65,6 +71,12 @@ __global__ void __launch_bounds__(kStepBX)
     if (a.pressure && (x == 0 || x == a.nx - 1))
       pressure_node<S, DYN>(fin, med, a, x, y, m[j].x, d[j]);
     const NodeState s = node_state<DYN>(d[j], m[j].x, m[j].y, a, k0[j]);
+    if (MOM) {
+      float *mo = mom + row + x;
+      mo[0] = s.drho_s;
+      mo[a.plane] = s.mx;
+      mo[2 * a.plane] = s.my;
+    }
     collide<S::kHiLo>(d[j], s, a);
     typename S::T *o = fout + row + x;
     const uint32_t h = SR ? mix32((uint32_t)(row + x) ^ ts) : 0u;
@@ -89,20 +101,30 @@ cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const
   __half *f16o = (__half *)fout;
   if (storage == 0) {
     if (dyn)
-      step_kernel<StoreF32, false, true><<<grid, block, 0, s>>>(a, f32i, f32o, med, tctr, k);
+      step_kernel<StoreF32, false, true><<<grid, block, 0, s>>>(a, f32i, f32o, med, tctr, k, nullptr);
     else
-      step_kernel<StoreF32, false, false><<<grid, block, 0, s>>>(a, f32i, f32o, med, tctr, k);
+      step_kernel<StoreF32, false, false><<<grid, block, 0, s>>>(a, f32i, f32o, med, tctr, k, nullptr);
   } else if (sr) {
     if (dyn)
-      step_kernel<StoreF16, true, true><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k);
+      step_kernel<StoreF16, true, true><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k, nullptr);
     else
-      step_kernel<StoreF16, true, false><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k);
+      step_kernel<StoreF16, true, false><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k, nullptr);
   } else {
     if (dyn)
-      step_kernel<StoreF16, false, true><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k);
+      step_kernel<StoreF16, false, true><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k, nullptr);
     else
-      step_kernel<StoreF16, false, false><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k);
+      step_kernel<StoreF16, false, false><<<grid, block, 0, s>>>(a, f16i, f16o, med, tctr, k, nullptr);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_moments(const StepArgs &a, int rows, const float *fin, float *fout,
+                                const float2 *med, float *mom, cudaStream_t s) {
+  if (rows <= 0 || a.nx <= 0) return cudaSuccess;
+  dim3 block(kStepBX);
+  dim3 grid((a.nx + kStepBX * kStepNPT - 1) / (kStepBX * kStepNPT), rows);
+  step_kernel<StoreF32, false, false, true><<<grid, block, 0, s>>>(a, fin, fout, med, nullptr, 0,
+                                                                   mom);
   return cudaGetLastError();
 }
 
@@ -202,78 +224,93 @@ __device__ __forceinline__ void block_reduce_store(double v[kNQ], double *partia
 }
 
 // ------------------------------------------- macroscopic / reduction kernel
+// Rows blockIdx.y, blockIdx.y + gridDim.y, ...: each thread adds the FP64
+// terms of its nodes one by one and takes part in one block reduction at
+// the end (FP64 arithmetic is slow on this GPU; a reduction tree per node
+// cost six times the per-node work).
 template <class S>
 __global__ void __launch_bounds__(kMacroBX)
     macro_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
                  const float2 *__restrict__ med, const MacroOut o) {
-  const int y = blockIdx.y;
   const int x = blockIdx.x * kMacroBX + threadIdx.x;
-  const bool wall = a.walls && (y == 0 || y == a.ny - 1);
   const long long n = (long long)a.nx * a.ny;
-  const long long j = (long long)y * a.nx + x;
   double v[kNQ] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  if (x < a.nx) {
+  for (int y = blockIdx.y; y < a.ny && x < a.nx; y += gridDim.y) {
+    const bool wall = a.walls && (y == 0 || y == a.ny - 1);
+    const long long j = (long long)y * a.nx + x;
     if (wall) {
       if (o.rho) o.rho[j] = 0.0;
       if (o.ux) o.ux[j] = 0.0;
       if (o.uy) o.uy[j] = 0.0;
       if (o.pops)
         for (int i = 0; i < 9; ++i) o.pops[i * n + j] = 0.0;
+      continue;
+    }
+    float d[9];
+    const long long jp = (long long)y * a.pitch + x;
+    const float2 m = med[jp];
+    pull_node<S>(fin, a, x, y, d);
+    const bool col = a.pressure && (x == 0 || x == a.nx - 1);
+    NodeState s;
+    if (a.kn0) {  // dynamic Kn
+      if (col) pressure_node<S, true>(fin, med, a, x, y, m.x, d);
+      s = node_state<true>(d, m.x, m.y, a, a.kn0[jp]);
     } else {
-      float d[9];
-      const long long jp = (long long)y * a.pitch + x;
-      const float2 m = med[jp];
-      pull_node<S>(fin, a, x, y, d);
-      const bool col = a.pressure && (x == 0 || x == a.nx - 1);
-      NodeState s;
-      if (a.kn0) {  // dynamic Kn
-        if (col) pressure_node<S, true>(fin, med, a, x, y, m.x, d);
-        s = node_state<true>(d, m.x, m.y, a, a.kn0[jp]);
+      if (col) pressure_node<S, false>(fin, med, a, x, y, m.x, d);
+      s = node_state<false>(d, m.x, m.y, a);
+    }
+    const float drho = s.drho_s * a.inv_scale;
+    if (o.rho) o.rho[j] = (double)s.rho;
+    if (o.ux) o.ux[j] = (double)s.ux;
+    if (o.uy) o.uy[j] = (double)s.uy;
+    if (o.pops) {
+      const double r0 = (double)a.rho0;
+      const double w[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                           1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+      const double is = (double)a.inv_scale;
+      for (int i = 0; i < 9; ++i) o.pops[i * n + j] = w[i] * r0 + (double)d[i] * is;
+    }
+    if (o.partials) {
+      const double ux = s.ux, uy = s.uy;
+      const bool finite = isfinite(s.ux) && isfinite(s.uy) && isfinite(s.rho);
+      if (finite) {
+        v[0] += ux;
+        v[1] += uy;
+        v[2] += (double)drho;
+        v[3] += ux * ux + uy * uy;
       } else {
-        if (col) pressure_node<S, false>(fin, med, a, x, y, m.x, d);
-        s = node_state<false>(d, m.x, m.y, a);
+        v[5] += 1.0;
       }
-      const float drho = s.drho_s * a.inv_scale;
-      (void)drho;
-      if (o.rho) o.rho[j] = (double)s.rho;
-      if (o.ux) o.ux[j] = (double)s.ux;
-      if (o.uy) o.uy[j] = (double)s.uy;
-      if (o.pops) {
-        const double r0 = (double)a.rho0;
-        const double w[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
-                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-        const double is = (double)a.inv_scale;
-        for (int i = 0; i < 9; ++i) o.pops[i * n + j] = w[i] * r0 + (double)d[i] * is;
-      }
-      if (o.partials) {
-        const double ux = s.ux, uy = s.uy;
-        const bool finite = isfinite(s.ux) && isfinite(s.uy) && isfinite(s.rho);
-        v[0] = finite ? ux : 0.0;
-        v[1] = finite ? uy : 0.0;
-        v[2] = finite ? (double)drho : 0.0;
-        v[3] = finite ? ux * ux + uy * uy : 0.0;
-        if (o.uprev) {
-          const long long jp = (long long)y * a.pitch + x;
-          const float2 up = o.uprev[jp];
-          const double dx = ux - (double)up.x, dy = uy - (double)up.y;
-          v[4] = finite ? dx * dx + dy * dy : 0.0;
-          if (o.update_prev) o.uprev[jp] = make_float2(s.ux, s.uy);
-        }
-        v[5] = finite ? 0.0 : 1.0;
+      if (o.uprev) {
+        const float2 up = o.uprev[jp];
+        const double dx = ux - (double)up.x, dy = uy - (double)up.y;
+        if (finite) v[4] += dx * dx + dy * dy;
+        if (o.update_prev) o.uprev[jp] = make_float2(s.ux, s.uy);
       }
     }
   }
   if (o.partials) block_reduce_store<kMacroBX>(v, o.partials);
 }
 
-int macro_blocks(const StepArgs &a) {
-  return ((a.nx + kMacroBX - 1) / kMacroBX) * a.ny;
+// Up to 16 blocks of 256 threads on each of 152 SMs.
+constexpr int kMacroMaxBlocks = 16 * 152;
+
+static dim3 macro_grid(const StepArgs &a) {
+  const int gx = (a.nx + kMacroBX - 1) / kMacroBX;
+  const int gy = std::max(1, std::min(a.ny, kMacroMaxBlocks / gx));
+  return dim3(gx, gy);
 }
+
+int macro_blocks(const StepArgs &a) {
+  const dim3 g = macro_grid(a);
+  return (int)(g.x * g.y);
+}
+
+int hist_blocks(const StepArgs &a) { return ((a.nx + kMacroBX - 1) / kMacroBX) * a.ny; }
 
 cudaError_t launch_macro(int storage, const StepArgs &a, const void *fin,
                          const float2 *med, const MacroOut &o, cudaStream_t s) {
-  dim3 block(kMacroBX);
-  dim3 grid((a.nx + kMacroBX - 1) / kMacroBX, a.ny);
+  const dim3 block(kMacroBX), grid = macro_grid(a);
   if (storage == 0)
     macro_kernel<StoreF32><<<grid, block, 0, s>>>(a, (const float *)fin, med, o);
   else
@@ -415,63 +452,154 @@ cudaError_t launch_histogram(int storage, const StepArgs &a, const void *fin, co
 }
 
 // ---------------------------------------------------------------- medium
+// f_c of Eq. 6-7 (b = -1; model 0) or of Eq. 4-5 (model 1) in FP32, for the
+// largest k_a of a dynamic-Kn medium (it only sets the FP16 scale).  Kn = 0
+// gives 1: Kn^-0.4348 = inf, alpha = 0 and Kn / (1 + Kn) = 0.
+__device__ __forceinline__ float fc_medium(float kn, int model) {
+  if (model == 1) return fmaf(4.0f, kn, 1.0f);
+  const float t = exp2f(-0.4348f * log2f(kn));
+  const float alpha = 1.358f / fmaf(0.170f, t, 1.0f);
+  const float r = kn < 1e30f ? kn / (1.0f + kn) : 1.0f;  // no inf / inf at huge Kn
+  return fmaf(alpha, kn, 1.0f) * fmaf(4.0f, r, 1.0f);
+}
+
+// 1 / k_a = 1 / (k_i f_c(Kn)) of Eq. 3 in FP64 with a single division.
+// Eq. 6-7 (b = -1) as one fraction: with t = Kn^-0.4348 and a = 1 + 0.17 t,
+//   1 + alpha Kn = (a + 1.358 Kn) / a,   1 + 4 Kn / (1 + Kn) = (1 + 5 Kn) / (1 + Kn),
+//   1 / k_a = a (1 + Kn) / (k_i (a + 1.358 Kn) (1 + 5 Kn)).
+// Only t comes from FP32 (log2f, exp2f: ~3e-7 relative); it enters through
+// a in both numerator and denominator, whose sensitivities nearly cancel:
+// d ln(1/k_a) / d ln t = 0.17 t 1.358 Kn / (a (a + 1.358 Kn)) <= 0.08, so
+// the FP32 1/k_a stored is within ~0.1 ulp of the FP64 value before its
+// final rounding.  FP64 runs at a small fraction of the FP32 rate on this
+// GPU: the FP64 power of Kn made the precompute 50 times slower than its
+// memory traffic.  Kn = 0 gives f_c = 1 exactly.
+__device__ __forceinline__ double inv_ka(double k, double K, int model) {
+  if (model == 1) return 1.0 / (k * fma(4.0, K, 1.0));
+  if (K == 0.0) return 1.0 / k;
+  const double t = (double)exp2f(-0.4348f * log2f((float)K));
+  const double a = fma(0.17, t, 1.0);
+  return (a * (1.0 + K)) / (k * fma(1.358, K, a) * fma(5.0, K, 1.0));
+}
+
+// Range checks on the bits of an FP64 value (integer comparisons; NaN
+// fails all of them).  0 <= e <= 1: the bits of a non-negative double order
+// as the value; -0 counts as 0.
+__device__ __forceinline__ bool in_unit_interval(double e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(e);
+  return b <= 0x3ff0000000000000ull || b == 0x8000000000000000ull;
+}
+// k > 0 (finite or +inf)
+__device__ __forceinline__ bool positive_or_inf(double k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(k);
+  return b >= 1ull && b <= 0x7ff0000000000000ull;
+}
+// K >= 0 and finite
+__device__ __forceinline__ bool nonneg_finite(double K) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(K);
+  return b < 0x7ff0000000000000ull || b == 0x8000000000000000ull;
+}
+
+// Grid-stride over rows: block b takes rows b, b + gridDim.x, ..., its
+// threads x, x + 256, ...  Each thread accumulates its nodes' partial sums
+// (one FP64 add per node: sum eps) and reduces them once at the end.
 __global__ void __launch_bounds__(kMediumBX)
     medium_kernel(const double *__restrict__ eps, const double *__restrict__ k_i,
                   const double *__restrict__ kn, int nx, int ny, int pitch, int y_lo,
-                  int y_hi, int kn_model, float *__restrict__ kn0, double kn_scale_max,
+                  int y_hi, int kn_model, float *__restrict__ kn0, float kn_scale_max,
                   float2 *__restrict__ med, unsigned *bad, double *__restrict__ partials) {
-  const int y = blockIdx.y;
-  const int x = blockIdx.x * kMediumBX + threadIdx.x;
-  double v[kNQ] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  if (x < nx) {
-    const long long j = (long long)y * nx + x;
-    float2 out = make_float2(0.0f, 0.0f);
-    float kn_out = 0.0f;
-    if (y >= y_lo && y < y_hi) {
-      const double e = eps[j], k = k_i[j], K = kn[j];
-      unsigned flags = 0;
-      if (!(e >= 0.0 && e <= 1.0)) flags |= 1u;               // also NaN
-      if (!(k > 0.0)) flags |= 2u;                             // NaN, <= 0
-      if (!(K >= 0.0 && isfinite(K))) flags |= 4u;
-      double inv_k = 0.0, ka_max = 0.0;
-      if (!flags) {
-        if (kn0) {  // dynamic Kn: 1/k_i stored, k_a formed at every step
-          if (!(k >= 1e-15)) flags |= 8u;
-          inv_k = isinf(k) ? 0.0 : 1.0 / k;
-          ka_max = k * fc_model(K * kn_scale_max, kn_model);  // at the lowest imposed pressure
-          kn_out = (float)K;
-        } else {
-          const double ka = k * fc_model(K, kn_model);         // Eq. 3 with Eq. 6-7 or 4-5
-          if (!(ka >= 1e-15)) flags |= 8u;                     // 1/k_a must fit FP32 math
-          inv_k = isinf(ka) ? 0.0 : 1.0 / ka;
-          ka_max = ka;
+  double se = 0.0;
+  unsigned nodes = 0, open = 0, flags = 0;
+  float ka_max = 0.0f;
+  for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+    const bool fluid_row = y >= y_lo && y < y_hi;
+    for (int x = threadIdx.x; x < nx; x += kMediumBX) {
+      const long long j = (long long)y * nx + x;
+      const long long jp = (long long)y * pitch + x;
+      float2 out = make_float2(0.0f, 0.0f);
+      float kn_out = 0.0f;
+      if (fluid_row) {
+        const double e = eps[j], k = k_i[j], K = kn[j];
+        unsigned f = 0;
+        if (!in_unit_interval(e)) f |= 1u;
+        if (!positive_or_inf(k)) f |= 2u;
+        if (!nonneg_finite(K)) f |= 4u;
+        const float ef = (float)e;
+        float inv_k = 0.0f, ka = 0.0f;
+        if (!f) {
+          if (kn0) {  // dynamic Kn: 1/k_i stored, k_a formed at every step
+            const float kf = (float)k, Kf = (float)K;
+            if (!(kf >= 1e-15f)) f |= 8u;
+            inv_k = 1.0f / kf;                                    // 0 for k_i = inf
+            ka = kf * fc_medium(Kf * kn_scale_max, kn_model);     // at the lowest pressure
+            kn_out = Kf;
+          } else {
+            const double inv = inv_ka(k, K, kn_model);            // Eq. 3 with Eq. 6-7 or 4-5
+            if (!(inv <= 1e15)) f |= 8u;                          // k_a >= 1e-15 (FP32 math)
+            inv_k = (float)inv;                                   // 0 for an open pore
+            ka = 1.0f / inv_k;
+          }
+        }
+        flags |= f;
+        out = make_float2(ef, inv_k);
+        se += e;
+        ++nodes;
+        if (!f && ef > 0.0f) {
+          if (inv_k > 0.0f) ka_max = fmaxf(ka_max, ka);  // largest finite k_a
+          else ++open;                                   // open pores (k_a = inf)
         }
       }
-      if (flags) atomicOr(bad, flags);
-      out = make_float2((float)e, (float)inv_k);
-      v[0] = e;
-      v[1] = 1.0;
-      if (!flags && e > 0.0) {
-        if (inv_k > 0.0) v[2] = ka_max;  // largest finite k_a (max-reduced)
-        else v[3] = 1.0;                 // open pores (k_a = inf)
-      }
+      med[jp] = out;
+      if (kn0) kn0[jp] = kn_out;
     }
-    med[(long long)y * pitch + x] = out;
-    if (kn0) kn0[(long long)y * pitch + x] = kn_out;
   }
+  if (flags) atomicOr(bad, flags);
+  double v[kNQ] = {se, (double)nodes, (double)ka_max, (double)open, 0.0, 0.0};
   block_reduce_store<kMediumBX>(v, partials, kMediumMaxMask);
 }
 
-int medium_blocks(int nx, int ny) { return ((nx + kMediumBX - 1) / kMediumBX) * ny; }
+// One block per row up to 8 resident blocks of 256 threads on each of 152
+// SMs; wider grids only add partials.
+constexpr int kMediumMaxBlocks = 8 * 152;
+int medium_blocks(int nx, int ny) {
+  (void)nx;
+  return ny < kMediumMaxBlocks ? ny : kMediumMaxBlocks;
+}
 
 cudaError_t launch_medium(const double *eps, const double *k_i, const double *kn,
                           int nx, int ny, int pitch, int y_lo, int y_hi, int kn_model,
                           float *kn0, double kn_scale_max, float2 *med, unsigned *bad,
                           double *partials, cudaStream_t s) {
-  dim3 block(kMediumBX);
+  medium_kernel<<<medium_blocks(nx, ny), kMediumBX, 0, s>>>(
+      eps, k_i, kn, nx, ny, pitch, y_lo, y_hi, kn_model, kn0, (float)kn_scale_max, med, bad,
+      partials);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- apparent permeability
+// k_a of every node of the fluid rows as the step sees it: 1 / (stored
+// 1/k_a), or with a dynamic Kn 1 / ((1/k_i) / f_c(Kn0)) at the pressure
+// p0 (q = 1) with the step's own FP32 f_c.  Plate rows read 0.
+__global__ void __launch_bounds__(kMediumBX)
+    ka_kernel(const float2 *__restrict__ med, const float *__restrict__ kn0, int nx, int ny,
+              int pitch, int y_lo, int y_hi, int kn_model, double *__restrict__ ka) {
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * kMediumBX + threadIdx.x;
+  if (x >= nx) return;
+  double v = 0.0;
+  if (y >= y_lo && y < y_hi) {
+    const long long jp = (long long)y * pitch + x;
+    float inv = med[jp].y;
+    if (kn0) inv = inv / fc_f32(kn0[jp], kn_model);
+    v = 1.0 / (double)inv;  // inf for an open pore (1/k_a = 0)
+  }
+  ka[(long long)y * nx + x] = v;
+}
+
+cudaError_t launch_ka(const float2 *med, const float *kn0, int nx, int ny, int pitch, int y_lo,
+                      int y_hi, int kn_model, double *ka, cudaStream_t s) {
   dim3 grid((nx + kMediumBX - 1) / kMediumBX, ny);
-  medium_kernel<<<grid, block, 0, s>>>(eps, k_i, kn, nx, ny, pitch, y_lo, y_hi, kn_model, kn0,
-                                       kn_scale_max, med, bad, partials);
+  ka_kernel<<<grid, kMediumBX, 0, s>>>(med, kn0, nx, ny, pitch, y_lo, y_hi, kn_model, ka);
   return cudaGetLastError();
 }
 

@@ -57,6 +57,11 @@ inline int row_pitch(int nx) {
 cudaError_t launch_step(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
                         void *fout, const float2 *med, const unsigned long long *tctr, int k,
                         cudaStream_t s);
+// The FP32 direct step (static Kn, no stochastic rounding) that also
+// stores every updated node's post-stream moments: rho - rho0, m_x, m_y in
+// three [ny][pitch] float planes at mom, a.plane apart (adjoint recompute).
+cudaError_t launch_step_moments(const StepArgs &a, int rows, const float *fin, float *fout,
+                                const float2 *med, float *mom, cudaStream_t s);
 // Vectorised FP16 variant of the same step (four nodes per thread).
 cudaError_t launch_wide(bool sr, const StepArgs &a, int rows, const void *fin, void *fout,
                         const float2 *med, const unsigned long long *tctr, int k,
@@ -81,6 +86,9 @@ cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s);
 
 // Blocks a macroscopic/reduction launch over all ny rows uses.
 int macro_blocks(const StepArgs &a);
+// Blocks (partials) of the histogram's first pass (one block per 256 nodes
+// of a row).
+int hist_blocks(const StepArgs &a);
 cudaError_t launch_macro(int storage, const StepArgs &a, const void *fin,
                          const float2 *med, const MacroOut &o, cudaStream_t s);
 
@@ -101,8 +109,13 @@ cudaError_t launch_medium(const double *eps, const double *k_i, const double *kn
                           float *kn0, double kn_scale_max, float2 *med, unsigned *bad,
                           double *partials, cudaStream_t s);
 
+// k_a per node as the step uses it ([ny][nx] float64; plate rows 0, open
+// pores +inf); with kn0 != NULL the k_a at the reference pressure.
+cudaError_t launch_ka(const float2 *med, const float *kn0, int nx, int ny, int pitch, int y_lo,
+                      int y_hi, int kn_model, double *ka, cudaStream_t s);
+
 // Normalised-velocity histogram: pass 1 writes the maximum of |u| over the
-// fluid rows of each macro block (macro_blocks(a) doubles, a.y0 ignored);
+// fluid rows of each block (hist_blocks(a) doubles, a.y0 ignored);
 // pass 2 adds the counts of bins min(floor(|u| / umax * nbins), nbins - 1)
 // to counts[0..nbins).  nbins <= kMaxHistBins.
 constexpr int kMaxHistBins = 64;

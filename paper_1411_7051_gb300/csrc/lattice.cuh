@@ -329,11 +329,15 @@ __device__ __forceinline__ NodeStateT<V> node_state_t(const V d[9], V eps, V inv
     }
   } else {
     static_assert(!DYN, "the pair path has a static Kn");
-    // both forms, then each lane keeps its own
+    const bool px = eps.x > 0.0f, py = eps.y > 0.0f;
+    if (px && py) {  // the common case: two permeable nodes
+      porous_state(s, eps, inv_k, c, a);
+      return s;
+    }
+    // otherwise both forms, then each lane keeps its own
     NodeStateT<V> q = s;
     porous_state(s, eps, inv_k, c, a);
     solid_state(q, c);
-    const bool px = eps.x > 0.0f, py = eps.y > 0.0f;
 #define LBMP_PICK(f) s.f = make_float2(px ? s.f.x : q.f.x, py ? s.f.y : q.f.y)
     LBMP_PICK(ieps);
     LBMP_PICK(ux);

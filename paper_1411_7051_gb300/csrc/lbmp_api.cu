@@ -51,7 +51,7 @@ lbmp_status cuda_fail(cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);      \
   } while (0)
 
-constexpr int kGraphSteps = 32;   // even, so a replay keeps the buffer parity
+constexpr int kGraphLevels = 6;   // step graphs of 1, 2, 4, ..., 32 steps
 constexpr uint64_t kStateMagic = 0x4c424d5053544131ull;  // "LBMPSTA1"
 
 struct StateHeader {
@@ -84,11 +84,12 @@ lbmp_status dalloc(lbmp_ctx *c, void **ptr, size_t bytes, const char *what) {
 }
 
 void free_graphs(lbmp_ctx *c) {
-  for (auto &g : c->graph)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (auto &level : c->graph)
+    for (auto &g : level)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
 }
 
 void release(lbmp_ctx *c) {
@@ -172,39 +173,26 @@ cudaError_t launch_one(lbmp_ctx *c, const StepArgs &a, const void *fin, void *fo
   return lbmp::launch_step(c->p.storage, c->sr, a, c->rows(), fin, fout, c->med, c->d_tctr, k, s);
 }
 
-// n single launches (time levels *tctr + 0 .. n-1), then the counter bump.
-lbmp_status launch_steps(lbmp_ctx *c, int64_t n) {
-  StepArgs a = c->args();
-  for (int64_t t = 0; t < n; ++t) {
-    LBMP_CK(launch_one(c, a, c->buf[c->cur], c->buf[c->cur ^ 1], (int)t, c->stream));
-    c->cur ^= 1;
-    c->launches++;
-  }
-  if (c->sr && n > 0) {
-    LBMP_CK(lbmp::launch_bump(c->d_tctr, (int)n, c->stream));
-    c->launches++;
-  }
-  return LBMP_OK;
-}
-
-// Graph of kGraphSteps steps starting from buffer `cur` (captured once per
+// Graph of 2^level steps starting from buffer `cur` (captured once per
 // medium: the launch arguments hold the storage scale), plus the counter
-// bump when the rounding is stochastic.
-lbmp_status get_graph(lbmp_ctx *c, int cur, cudaGraphExec_t *out) {
-  if (c->graph[cur]) {
-    *out = c->graph[cur];
+// bump when the rounding is stochastic.  A replay saves the launch gaps of
+// single launches (~3 us per step at 4096^2).
+lbmp_status get_graph(lbmp_ctx *c, int level, int cur, cudaGraphExec_t *out) {
+  if (c->graph[level][cur]) {
+    *out = c->graph[level][cur];
     return LBMP_OK;
   }
+  const int nsteps = 1 << level;
   StepArgs a = c->args();
   cudaGraph_t g = nullptr;
   LBMP_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   int b = cur;
   cudaError_t err = cudaSuccess;
-  for (int t = 0; t < kGraphSteps && err == cudaSuccess; ++t) {
+  for (int t = 0; t < nsteps && err == cudaSuccess; ++t) {
     err = launch_one(c, a, c->buf[b], c->buf[b ^ 1], t, c->cap_stream);
     b ^= 1;
   }
-  if (err == cudaSuccess && c->sr) err = lbmp::launch_bump(c->d_tctr, kGraphSteps, c->cap_stream);
+  if (err == cudaSuccess && c->sr) err = lbmp::launch_bump(c->d_tctr, nsteps, c->cap_stream);
   cudaError_t end = cudaStreamEndCapture(c->cap_stream, &g);
   if (err != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -215,7 +203,7 @@ lbmp_status get_graph(lbmp_ctx *c, int cur, cudaGraphExec_t *out) {
   cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
   cudaGraphDestroy(g);
   if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
-  c->graph[cur] = exec;
+  c->graph[level][cur] = exec;
   *out = exec;
   return LBMP_OK;
 }
@@ -393,7 +381,8 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     if (e != cudaSuccess) LBMP_TRY(cuda_fail(e, "cudaStreamCreate (capture)"));
     StepArgs a = c->args();
     a.y0 = 0;
-    c->partials_blocks = std::max(lbmp::macro_blocks(a), lbmp::medium_blocks(p.nx, p.ny));
+    c->partials_blocks = std::max({lbmp::macro_blocks(a), lbmp::hist_blocks(a),
+                                   lbmp::medium_blocks(p.nx, p.ny)});
     LBMP_TRY(dalloc(c, &c->buf[0], c->buf_bytes(), "population buffer A"));
     LBMP_TRY(dalloc(c, &c->buf[1], c->buf_bytes(), "population buffer B"));
     LBMP_TRY(dalloc(c, (void **)&c->med, (size_t)c->plane * sizeof(float2), "medium"));
@@ -537,17 +526,22 @@ lbmp_status lbmp_step(lbmp_ctx *c, int64_t n) {
     if (n == 0) return LBMP_OK;
     lbmp_status st = set_device(c);
     if (st) return st;
+    // n = 32 q + sum of binary digits: q replays of the 32-step graph, then
+    // one replay of each smaller power of two
     int64_t left = n;
-    while (left >= kGraphSteps) {
-      cudaGraphExec_t g = nullptr;
-      st = get_graph(c, c->cur, &g);
-      if (st) return st;
-      LBMP_CK(cudaGraphLaunch(g, c->stream));
-      c->launches += kGraphSteps + (c->sr ? 1 : 0);
-      left -= kGraphSteps;
+    for (int level = kGraphLevels - 1; level >= 0 && left > 0; --level) {
+      const int64_t size = 1ll << level;
+      while (left >= size) {
+        cudaGraphExec_t g = nullptr;
+        st = get_graph(c, level, c->cur, &g);
+        if (st) return st;
+        LBMP_CK(cudaGraphLaunch(g, c->stream));
+        c->launches += size + (c->sr ? 1 : 0);
+        if (size & 1) c->cur ^= 1;  // an odd replay swaps the buffers
+        left -= size;
+        if (level < kGraphLevels - 1) break;  // one replay of each smaller size
+      }
     }
-    st = launch_steps(c, left);
-    if (st) return st;
     c->steps += n;
     return LBMP_OK;
   } catch (...) {
@@ -597,6 +591,33 @@ lbmp_status lbmp_macroscopic(lbmp_ctx *c, double *rho, double *ux, double *uy,
     return LBMP_OK;
   } catch (...) {
     return fail(LBMP_ECUDA, "lbmp_macroscopic: unexpected exception");
+  }
+}
+
+lbmp_status lbmp_apparent_permeability(lbmp_ctx *c, double *ka, int32_t where) {
+  try {
+    if (!c || !ka) return fail(LBMP_EINVAL, "lbmp_apparent_permeability: NULL argument");
+    if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
+    if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_apparent_permeability: no fields set");
+    lbmp_status st = set_device(c);
+    if (st) return st;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    DevTemp tmp;
+    double *out = ka;
+    if (where == LBMP_HOST) {
+      cudaError_t e = cudaMalloc(&tmp.ptr, n * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+      out = (double *)tmp.ptr;
+    }
+    LBMP_CK(lbmp::launch_ka(c->med, c->kn0, c->p.nx, c->p.ny, c->pitch, c->y_lo, c->y_hi,
+                            c->p.kn_model, out, c->stream));
+    c->launches++;
+    if (where == LBMP_HOST)
+      LBMP_CK(cudaMemcpyAsync(ka, out, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBMP_CK(cudaStreamSynchronize(c->stream));
+    return LBMP_OK;
+  } catch (...) {
+    return fail(LBMP_ECUDA, "lbmp_apparent_permeability: unexpected exception");
   }
 }
 
@@ -694,7 +715,7 @@ lbmp_status lbmp_velocity_histogram(lbmp_ctx *c, int32_t nbins, double *umax,
     a.y0 = 0;
     LBMP_CK(lbmp::launch_speed_max(c->p.storage, a, c->buf[c->cur], c->med, c->partials,
                                    c->stream));
-    LBMP_CK(lbmp::launch_finalize(c->partials, lbmp::macro_blocks(a), 1, c->results, c->stream,
+    LBMP_CK(lbmp::launch_finalize(c->partials, lbmp::hist_blocks(a), 1, c->results, c->stream,
                                   1u));
     LBMP_CK(cudaMemcpyAsync(c->h_results, c->results, sizeof(double), cudaMemcpyDeviceToHost,
                             c->stream));

@@ -125,6 +125,8 @@ def load(path: str = LIB_PATH):
     L.lbmp_macroscopic.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int32]
     L.lbmp_populations.restype = st
     L.lbmp_populations.argtypes = [_VP, _VP, ctypes.c_int32]
+    L.lbmp_apparent_permeability.restype = st
+    L.lbmp_apparent_permeability.argtypes = [_VP, _VP, ctypes.c_int32]
     L.lbmp_set_populations.restype = st
     L.lbmp_set_populations.argtypes = [_VP, _VP, ctypes.c_int32]
     L.lbmp_permeability.restype = st
@@ -389,6 +391,13 @@ class Sim:
         uy, pv, _ = self._out_field(shape, device)
         _check(load().lbmp_macroscopic(self._h, pr, pu, pv, w))
         return rho, ux, uy
+
+    def apparent_permeability(self, device: bool = True):
+        """``lbmp_apparent_permeability``: k_a of every node as the step uses
+        it (Eq. 3), [ny, nx] float64; plate rows 0, open pores inf."""
+        ka, pk, w = self._out_field((self.ny, self.nx), device)
+        _check(load().lbmp_apparent_permeability(self._h, pk, w))
+        return ka
 
     def populations(self, device: bool = True):
         f, pf, w = self._out_field((9, self.ny, self.nx), device)

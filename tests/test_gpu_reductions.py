@@ -9,9 +9,11 @@ Two comparisons per case:
     given, as its snapshot, the FP32 velocity the GPU stored at its own
     snapshot.  What differs is then only the GPU's FP32 velocity arithmetic
     (~1e-7 relative per node) and the summation order, so the residual
-    (of order 0.1 - 1 here) agrees to 1e-6 relative and the mass, whose
-    per-node FP32 density rounding (~6e-8 of a deviation of ~1e-3) averages
-    out, to 1e-12;
+    (of order 0.1 - 1 here) agrees to 1e-6 relative.  The mass agrees to
+    1e-11 relative: the GPU's per-node FP32 density rounding (~6e-8 of a
+    deviation of ~1e-3) averages out, and the oracle adds its 9 N
+    populations one by one in FP64, whose rounding is bounded by
+    9 N 2^-53 relative (9e-12 for N = 9216; measured ~2e-13);
   * same run: both sides step from rest; the FP32 trajectory drifts from
     the FP64 one by the velocity bound of the step parity tests (rel-L2 <=
     1e-5), so the residual agrees to 1e-4 relative and the mass to 1e-9.
@@ -76,7 +78,7 @@ def test_residual_and_mass_same_state(orc, name, storage):
          storage="fp32" if storage == FP32 else "fp16")
     assert 1e-3 < r_orc < 2.0
     assert e_r <= 1e-6, (r_gpu, r_orc)
-    assert e_m <= 1e-12, (m_gpu, m_orc)
+    assert e_m <= 1e-11, (m_gpu, m_orc)
 
 
 @pytest.mark.parametrize("name", list(_cases()))
@@ -86,7 +88,7 @@ def test_residual_and_mass_same_run(orc, name):
     osim = oracle_sim(orc, case)
     gs.residual()
     _, oux, ouy = osim.macroscopic()
-    assert gs.mass() == pytest.approx(osim.mass(), rel=1e-13, abs=0)   # rest state
+    assert gs.mass() == pytest.approx(osim.mass(), rel=1e-11, abs=0)   # rest state
     for n in (200, 300):
         gs.step(n)
         osim.step(n)
