@@ -30,6 +30,8 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <map>
+#include <tuple>
 
 #include "context.h"
 #include "kernels.h"
@@ -445,14 +447,50 @@ struct DevBuf {
     }                                                                                    \
   } while (0)
 
-// One forward step with the kernel the context selected.
-cudaError_t forward_step(lbmp_ctx *c, const lbmp::StepArgs &a, const void *fin, void *fout,
-                         cudaStream_t s) {
-  if (c->staged)
-    return lbmp::launch_staged(c->p.storage, false, a, c->rows(), fin, fout, c->med, c->d_tctr,
-                               0, c->d_err, c->nsm, s);
-  return lbmp::launch_step(c->p.storage, false, a, c->rows(), fin, fout, c->med, c->d_tctr, 0, s);
+// The launches of one backward segment: n recompute steps from the
+// checkpoint copy in seg[0] (the two state buffers alternate; level t's
+// moments go to mom + t * mom_level), then the n reverse steps from the
+// last level down, with an FP64 fold after every kFold-th reverse step of
+// the whole sweep (`reversed` of them done before this segment).  lam[0]
+// holds Lambda^{t+1} of the segment's last level on entry.
+cudaError_t enqueue_segment(const lbmp::AdjArgs &A0, int rows, const float2 *med, char *segp,
+                            size_t state, char *momp, size_t mom_level, int64_t n,
+                            float *const lam[2], int64_t reversed, cudaStream_t s) {
+  lbmp::AdjArgs A = A0;
+  const lbmp::StepArgs &a = A.a;
+  cudaError_t e = cudaSuccess;
+  for (int64_t t = 0; t < n && e == cudaSuccess; ++t)
+    e = lbmp::launch_step_moments(a, rows, (const float *)(segp + state * (t & 1)),
+                                  (float *)(segp + state * ((t + 1) & 1)), med,
+                                  (float *)(momp + mom_level * t), s);
+  const dim3 blk(lbmp::kAdjBX), grd((a.nx + lbmp::kAdjBX - 1) / lbmp::kAdjBX, rows);
+  int next = 0;
+  for (int64_t t = n - 1; t >= 0 && e == cudaSuccess; --t) {
+    A.lam_in = lam[next];
+    A.lam_out = lam[next ^ 1];
+    A.fin = nullptr;
+    A.mom = (const float *)(momp + mom_level * t);
+    lbmp::adjoint_step_kernel<false><<<grd, blk, 0, s>>>(A);
+    e = cudaGetLastError();
+    next ^= 1;
+    if (e == cudaSuccess && ++reversed % lbmp::kFold == 0) {
+      lbmp::adjoint_fold_kernel<<<grd, blk, 0, s>>>(A);
+      e = cudaGetLastError();
+    }
+  }
+  return e;
 }
+
+// Instantiated backward-segment graphs of one gradient call, keyed by the
+// segment length, which adjoint buffer holds Lambda^{t+1} on entry, and
+// the fold phase (reversed steps mod kFold): full segments share one graph
+// per phase, so a call captures at most kFold + 1 of them.
+struct SegmentGraphs {
+  std::map<std::tuple<int64_t, int, int>, cudaGraphExec_t> g;
+  ~SegmentGraphs() {
+    for (auto &kv : g) cudaGraphExecDestroy(kv.second);
+  }
+};
 
 }  // namespace
 
@@ -500,23 +538,19 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
     double *g_eps = (double *)grad.p, *g_lk = (double *)((char *)grad.p + field);
     float2 *acc = (float2 *)((char *)grad.p + 2 * field);
 
-    // forward pass from rest in the context's own buffers, checkpointing
-    // the first level of every segment
+    // forward pass from rest in the context's own buffers (the step graphs
+    // of lbmp_step), checkpointing the first level of every segment
     ACK(cudaMemsetAsync(c->buf[0], 0, state, s));
     ACK(cudaMemsetAsync(c->buf[1], 0, state, s));
     ACK(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), s));
-    int cur = 0;
+    c->cur = 0;
+    c->steps = 0;
     for (int64_t sg = 0; sg < nseg; ++sg) {
-      ACK(cudaMemcpyAsync(ckp + state * sg, c->buf[cur], state, cudaMemcpyDeviceToDevice, s));
-      const int64_t n = std::min(every, nsteps - sg * every);
-      for (int64_t t = 0; t < n; ++t) {
-        ACK(forward_step(c, a, c->buf[cur], c->buf[cur ^ 1], s));
-        cur ^= 1;
-      }
+      ACK(cudaMemcpyAsync(ckp + state * sg, c->buf[c->cur], state, cudaMemcpyDeviceToDevice, s));
+      lbmp_status fst = lbmp_step(c, std::min(every, nsteps - sg * every));
+      if (fst) return fst;
     }
-    c->cur = cur;
-    c->steps = nsteps;
-    c->launches += nsteps;
+    const int cur = c->cur;
     // J = k_g of level N, exactly as lbmp_permeability reports it
     double J = 0.0;
     lbmp_status st = lbmp_permeability(c, &J, nullptr);
@@ -546,31 +580,36 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
     ACK(cudaGetLastError());
     // backward, one segment at a time: recompute its levels from the
     // checkpoint (keeping only their moments), then run the reverse steps
-    // over them
-    float *lam_next = lam0, *lam_prev = lam1;  // Lambda^{t+1}, Lambda^t
-    int64_t reversed = 0;  // the FP32 accumulators fold every kFold reverse steps
+    // over them; each segment replays a captured graph
+    float *lams[2] = {lam0, lam1};  // lams[0]: Lambda^{t+1} of the next reverse step
+    int64_t reversed = 0;          // the FP32 accumulators fold every kFold reverse steps
+    SegmentGraphs graphs;
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
       const int64_t t0 = sg * every, n = std::min(every, nsteps - t0);
       ACK(cudaMemcpyAsync(segp, ckp + state * sg, state, cudaMemcpyDeviceToDevice, s));
-      for (int64_t t = 0; t < n; ++t)
-        ACK(lbmp::launch_step_moments(a, rows, (const float *)(segp + state * (t & 1)),
-                                      (float *)(segp + state * ((t + 1) & 1)), c->med,
-                                      (float *)(momp + mom_level * t), s));
-      for (int64_t t = n - 1; t >= 0; --t) {
-        A.lam_in = lam_next;
-        A.lam_out = lam_prev;
-        A.fin = nullptr;
-        A.mom = (const float *)(momp + mom_level * t);
-        lbmp::adjoint_step_kernel<false><<<grd, blk, 0, s>>>(A);
-        ACK(cudaGetLastError());
-        std::swap(lam_next, lam_prev);
-        if (++reversed % lbmp::kFold == 0) {
-          lbmp::adjoint_fold_kernel<<<grd, blk, 0, s>>>(A);
-          ACK(cudaGetLastError());
-          c->launches++;
+      const auto key = std::make_tuple(n, lams[0] == lam0 ? 0 : 1, (int)(reversed % lbmp::kFold));
+      auto it = graphs.g.find(key);
+      if (it == graphs.g.end()) {
+        cudaGraph_t g = nullptr;
+        ACK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = enqueue_segment(A, rows, c->med, segp, state, momp, mom_level, n, lams,
+                                         reversed, c->cap_stream);
+        cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          ACK(ce != cudaSuccess ? ce : ee);
         }
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        ACK(ie);
+        it = graphs.g.emplace(key, exec).first;
       }
-      c->launches += 2 * n;
+      ACK(cudaGraphLaunch(it->second, s));
+      const int64_t folds = (reversed + n) / lbmp::kFold - reversed / lbmp::kFold;
+      c->launches += 2 * n + folds;
+      reversed += n;
+      if (n & 1) std::swap(lams[0], lams[1]);
     }
     lbmp::adjoint_fold_kernel<<<grd, blk, 0, s>>>(A);
     ACK(cudaGetLastError());
