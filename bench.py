@@ -585,8 +585,12 @@ def adjoint_object(r, peak, peak_kind):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
                      "bytes_per_update": ADJOINT_BYTES_PER_NODE,
-                     "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-                     "traffic_per_update": (tr["dram_bytes_per_launch"] / tr["nodes"] if tr else None),
+                     "traffic": None,
+                     "reverse_kernel": {
+                         "bytes_per_update": ADJOINT_REVERSE_BYTES,
+                         "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                         "traffic_per_update": (tr["dram_bytes_per_launch"] / tr["nodes"]
+                                                if tr else None)},
                      "kernel": "lbmp::step_kernel<StoreF32, 0, 0, 1> (recompute with moments) + "
                                "lbmp::adjoint_step_kernel<false> (+ fold)",
                      "timing": "backward sweep (recompute + reverse) = gradient minus the "

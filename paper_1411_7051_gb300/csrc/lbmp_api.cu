@@ -210,6 +210,18 @@ lbmp_status get_graph(lbmp_ctx *c, int level, int cur, cudaGraphExec_t *out) {
 
 bool valid_where(int32_t w) { return w == LBMP_HOST || w == LBMP_DEVICE; }
 
+// The device address of a pinned, device-mapped host array, if it is one.
+bool mapped_host(const double *p, const double **dev) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return false;
+  *dev = static_cast<const double *>(at.devicePointer);
+  return true;
+}
+
 }  // namespace
 
 lbmp_status lbmp::validate_params(lbmp_params *p) {
@@ -427,7 +439,15 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
     const size_t n = (size_t)p.nx * p.ny;
     const double *de = eps, *dk = k_i, *dn = kn;
     DevTemp tmp;
+    // Host arrays in pinned, device-mapped memory are read by the kernel in
+    // place (over the CPU-GPU link); other host memory is staged.
+    if (where == LBMP_HOST && mapped_host(eps, &de) && mapped_host(k_i, &dk) &&
+        mapped_host(kn, &dn))
+      where = LBMP_DEVICE;
     if (where == LBMP_HOST) {
+      de = eps;
+      dk = k_i;
+      dn = kn;
       cudaError_t e = cudaMalloc(&tmp.ptr, 3 * n * sizeof(double));
       if (e != cudaSuccess) return cuda_fail(e, "staging buffer for the medium");
       double *t = (double *)tmp.ptr;
@@ -498,11 +518,12 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
         s = (int)std::floor(std::log2(1024.0 / dev));
         s = std::min(60, std::max(-60, s));
       }
-      c->scale = std::ldexp(1.0, s);
+      const double scale = std::ldexp(1.0, s);
+      if (scale != c->scale) free_graphs(c);  // the graphs' step arguments hold S
+      c->scale = scale;
     } else {
       c->scale = 1.0;
     }
-    free_graphs(c);
     LBMP_CK(cudaMemsetAsync(c->buf[0], 0, c->buf_bytes(), c->stream));
     LBMP_CK(cudaMemsetAsync(c->buf[1], 0, c->buf_bytes(), c->stream));
     LBMP_CK(cudaMemsetAsync(c->uprev, 0, (size_t)c->plane * sizeof(float2), c->stream));

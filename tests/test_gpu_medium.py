@@ -100,3 +100,28 @@ def test_medium_rejects_bad_values_and_keeps_the_mean_porosity(orc):
         n[4, 4] = -0.0
         sim.set_fields(e, m.k_i, n)
         assert sim.info().eps_mean == pytest.approx(e.mean(), rel=1e-14, abs=0)
+
+
+def test_pinned_host_inputs_match_pageable_ones():
+    """Pinned, device-mapped host arrays are read by the precompute in place;
+    the medium, and the run from it, are those of pageable host arrays."""
+    import torch
+    m = media.random_medium(130, 40, seed=6, p_open=0.1, p_solid=0.1)
+    ny, nx = m.eps.shape
+    cfg = lbmp.SimConfig(nx, ny, bc_x=lbmp.BCX_PRESSURE, bc_y=lbmp.BCY_WALLS, rho_in=1.001,
+                         rho_out=0.999, forchheimer=1)
+    pinned = [torch.from_numpy(np.ascontiguousarray(f)).pin_memory() for f in (m.eps, m.k_i, m.kn)]
+    with lbmp.Sim(cfg) as a, lbmp.Sim(cfg) as b:
+        a.set_fields(m.eps, m.k_i, m.kn)
+        b.set_fields(*pinned)
+        assert np.array_equal(a.apparent_permeability(False).numpy(),
+                              b.apparent_permeability(False).numpy())
+        assert a.info().eps_mean == b.info().eps_mean
+        a.step(30)
+        b.step(30)
+        assert np.array_equal(a.populations(False).numpy(), b.populations(False).numpy())
+        bad = pinned[0].clone().pin_memory()
+        bad[3, 4] = 2.0   # out of range: rejected as from pageable memory
+        with pytest.raises(lbmp.LbmpError) as ei:
+            b.set_fields(bad, pinned[1], pinned[2])
+        assert ei.value.status == lbmp.EINVAL
