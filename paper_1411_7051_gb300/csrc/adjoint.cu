@@ -370,7 +370,24 @@ __global__ void __launch_bounds__(kAdjBX, 8) adjoint_step_kernel(const AdjArgs A
     for (int i = 0; i < 9; ++i) mu[i] = 0.0f;
   } else {
     float lp[9];
-    reverse_pull(A, x, y, lp);
+    // Away from the lattice edges every destination z + e_i is a plain fluid
+    // node at a fixed offset; the edge rules of reverse_pull apply to the rest.
+    const bool inner = x >= 2 && x <= a.nx - 3 && y >= 2 && y <= a.ny - 3;
+    if (inner) {
+      const float *l = A.lam_in + j;
+      const long long P = a.plane, R = a.pitch;
+      lp[0] = l[0];
+      lp[1] = l[P + 1];
+      lp[2] = l[2 * P + R];
+      lp[3] = l[3 * P - 1];
+      lp[4] = l[4 * P - R];
+      lp[5] = l[5 * P + R + 1];
+      lp[6] = l[6 * P + R - 1];
+      lp[7] = l[7 * P - R - 1];
+      lp[8] = l[8 * P - R + 1];
+    } else {
+      reverse_pull(A, x, y, lp);
+    }
     collide_adjoint(lp, rho, mx, my, m.x, m.y, a, b);
 #pragma unroll
     for (int i = 0; i < 9; ++i) mu[i] = a.one_m_omega * lp[i];
