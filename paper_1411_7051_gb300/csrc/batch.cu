@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(batch_threads<S>(), 1)
       if (x == 0 || x + 2 >= a.nx) continue;  // column edges: the pass below
       const float4 m = *reinterpret_cast<const float4 *>(sm + c);
       if (a.walls && (y == 1 || y == a.ny - 2)) {
-        staged_edge_pair<S, SR, C>(sp, fin, fout, med, a, c, x, y, m, tsi);
+        staged_edge_pair_packed<S, SR, C>(sp, fin, fout, med, a, c, x, y, m, tsi);
         continue;
       }
       staged_interior_pair<S, SR, C>(sp, fout, a, c, x, y, m, tsi);

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kStepBX)
                 typename S::T *__restrict__ fout, const float2 *__restrict__ med,
                 const unsigned long long *__restrict__ tctr, int k,
                 float *__restrict__ mom) {
-  const int y = a.y0 + blockIdx.y;
+  const int y = a.y0 + (a.rev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y);
   const int xb = blockIdx.x * (kStepBX * kStepNPT) + threadIdx.x;
   const long long row = (long long)y * a.pitch;
   float d[kStepNPT][9];
@@ -482,6 +482,133 @@ __device__ __forceinline__ double inv_ka(double k, double K, int model) {
   return (a * (1.0 + K)) / (k * fma(1.358, K, a) * fma(5.0, K, 1.0));
 }
 
+// ---- the same fraction in FP32-pair arithmetic (value = hi + lo) ----------
+// FP64 instructions are the bottleneck of the precompute on this GPU, so
+// for the usual ranges of k_i and Kn the fraction is evaluated with pairs
+// of FP32 numbers carrying ~44 significant bits: exact sums (Knuth's
+// two-sum) and exact products (fma of the product and its negation), the
+// standard error-free transformations.  Beside the FP32 power of Kn (as in
+// inv_ka) the result differs from the FP64 one by ~2^-40 before its final
+// rounding to FP32.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+  F2 s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ F2 f2_mul(F2 x, F2 y) {
+  F2 p = two_prod(x.hi, y.hi);
+  const float c = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+  return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
+}
+// n / d from an approximate reciprocal r of d.hi (relative error e ~ 2^-23):
+// q1 = n.hi r is off by ~e, the remainder n - q1 d is formed exactly enough
+// (~2^-48 of n), and its quotient by the same r corrects q1 to a relative
+// error of order e^2 -- one Newton step on the quotient.
+__device__ __forceinline__ F2 f2_div(F2 n, F2 d) {
+  const float r = rcp_approx(d.hi);
+  const float q1 = __fmul_rn(n.hi, r);
+  const F2 qd = f2_mul({q1, 0.0f}, d);           // q1 d
+  const F2 rem = f2_add(n, {-qd.hi, -qd.lo});     // n - q1 d
+  return fast_two_sum(q1, __fmul_rn(rem.hi, r));
+}
+// A double in [2^-60, 2^60] (not 0) as hi + lo with integer operations only: hi
+// keeps the leading 24 bits, lo the next 29 (rounded to 24; the pair then
+// carries d to a relative 2^-48).
+__device__ __forceinline__ F2 f2_from_double(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;             // unbiased exponent
+  const unsigned hib = (unsigned)((b >> 32) & 0x80000000u) |  // sign
+                       ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
+  const float lo_int = (float)(unsigned)(b & 0x1fffffffull);  // the low 29 mantissa bits
+  const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);  // 2^(e - 52)
+  return {__uint_as_float(hib), (b >> 63) ? -lo_int * scale : lo_int * scale};
+}
+
+// Kn^-0.4348 for Kn in [1e-12, 1e6] from the hardware base-2 logarithm and
+// power (lg2.approx: absolute error ~2^-22.6, the exponent part exact;
+// ex2.approx: relative ~2^-22.5).  The exponent y = -0.4348 log2 Kn (|y| up
+// to 17) is carried as y_hi + y_lo (exact product, the constant as hi + lo)
+// and 2^y = 2^y_hi (1 + ln2 y_lo): ~3e-7 relative in all, where rounding y
+// to one FP32 would alone cost up to 7e-7.  t enters the fraction with a
+// sensitivity below 0.08.
+__device__ __forceinline__ float kn_power(float K) {
+  constexpr float c_hi = -0.4348f;
+  constexpr float c_lo = (float)(-0.4348 - (double)c_hi);
+  float lg, t;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(K));
+  const float y_hi = __fmul_rn(lg, c_hi);
+  const float y_lo = __fmaf_rn(lg, c_lo, __fmaf_rn(lg, c_hi, -y_hi));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(y_hi));
+  return __fmaf_rn(__fmul_rn(t, 0.69314718f), y_lo, t);
+}
+
+// 1 / k_a of inv_ka() for k_i and Kn in the ranges FP32 pairs hold
+// comfortably (k_i in [1e-16, 1e12], Kn in [1e-12, 1e6] or 0; the others
+// take the FP64 fraction): FP32 to within the FP32 power's error.  k > 0
+// and K >= 0 (or -0) on entry, so the range tests compare bit patterns: the
+// bits of non-negative doubles order as their values (FP64 compares are
+// as slow as the rest of FP64 on this GPU).
+__device__ __forceinline__ float inv_ka_pair(double k, double K, int model) {
+  const unsigned long long kb = (unsigned long long)__double_as_longlong(k);
+  const unsigned long long Kb = (unsigned long long)__double_as_longlong(K) << 1;  // sign dropped
+  const bool K0 = Kb == 0;
+  const bool k_ok = kb >= 0x3c9cd2b297d889bcull && kb <= 0x426d1a94a2000000ull;  // [1e-16, 1e12]
+  const bool K_ok = K0 || (Kb >= (0x3d719799812dea11ull << 1) &&
+                           Kb <= (0x412e848000000000ull << 1));                  // [1e-12, 1e6]
+  if (!k_ok || !K_ok) return (float)inv_ka(k, K, model);
+  const F2 kk = f2_from_double(k);
+  const F2 one = {1.0f, 0.0f};
+  if (K0) {  // f_c = 1 in both models
+    const F2 q = f2_div(one, kk);
+    return __fadd_rn(q.hi, q.lo);
+  }
+  if (model == 1) {  // 1 / (k (1 + 4 Kn))
+    const F2 KK = f2_from_double(K);
+    const F2 den = f2_mul(kk, f2_add(one, f2_mul({4.0f, 0.0f}, KK)));
+    const F2 q = f2_div(one, den);
+    return __fadd_rn(q.hi, q.lo);
+  }
+  const F2 KK = f2_from_double(K);
+  const float t = kn_power(KK.hi);  // Kn^-0.4348
+  const F2 c017 = {0.17f, (float)(0.17 - (double)0.17f)};
+  const F2 c1358 = {1.358f, (float)(1.358 - (double)1.358f)};
+  const F2 a = f2_add(one, f2_mul(c017, {t, 0.0f}));  // 1 + 0.17 t
+  const F2 num = f2_mul(a, f2_add(one, KK));
+  const F2 den = f2_mul(f2_mul(kk, f2_add(a, f2_mul(c1358, KK))),
+                        f2_add(one, f2_mul({5.0f, 0.0f}, KK)));
+  const F2 q = f2_div(num, den);
+  return __fadd_rn(q.hi, q.lo);
+}
+
+// A double in [2^-126, 1] rounded to the nearest FP32 (ties to even) with
+// integer operations; the rest (0, and values too small for a normal FP32)
+// by the FP64 conversion.
+__device__ __forceinline__ float unit_to_float(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < -126) return (float)d;
+  const unsigned rest = (unsigned)(b & 0x1fffffffull);  // the 29 bits dropped
+  unsigned f = ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
+  if (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ++f;  // carries into the exponent
+  return __uint_as_float(f);
+}
+
 // Range checks on the bits of an FP64 value (integer comparisons; NaN
 // fails all of them).  0 <= e <= 1: the bits of a non-negative double order
 // as the value; -0 counts as 0.
@@ -500,17 +627,24 @@ __device__ __forceinline__ bool nonneg_finite(double K) {
   return b < 0x7ff0000000000000ull || b == 0x8000000000000000ull;
 }
 
+// One block per row up to 5 resident blocks of 256 threads on each of 152
+// SMs (the launch bound keeps all of them resident); wider grids only add
+// partials.
+constexpr int kMediumMaxBlocks = 5 * 152;
+
 // Grid-stride over rows: block b takes rows b, b + gridDim.x, ..., its
 // threads x, x + 256, ...  Each thread accumulates its nodes' partial sums
 // (one FP64 add per node: sum eps) and reduces them once at the end.
-__global__ void __launch_bounds__(kMediumBX)
+__global__ void __launch_bounds__(kMediumBX, kMediumMaxBlocks / 152)
     medium_kernel(const double *__restrict__ eps, const double *__restrict__ k_i,
                   const double *__restrict__ kn, int nx, int ny, int pitch, int y_lo,
                   int y_hi, int kn_model, float *__restrict__ kn0, float kn_scale_max,
                   float2 *__restrict__ med, unsigned *bad, double *__restrict__ partials) {
-  double se = 0.0;
+  F2 se = {0.0f, 0.0f};  // sum of eps: FP32 pairs (~44 bits) without FP64 arithmetic
+  double se_small = 0.0;  // and the few eps below 2^-60
   unsigned nodes = 0, open = 0, flags = 0;
-  float ka_max = 0.0f;
+  float ka_max = 0.0f;         // dynamic Kn: the largest finite k_a
+  float inv_min = INFINITY;    // static Kn: the smallest positive 1/k_a
   for (int y = blockIdx.x; y < ny; y += gridDim.x) {
     const bool fluid_row = y >= y_lo && y < y_hi;
     for (int x = threadIdx.x; x < nx; x += kMediumBX) {
@@ -524,7 +658,7 @@ __global__ void __launch_bounds__(kMediumBX)
         if (!in_unit_interval(e)) f |= 1u;
         if (!positive_or_inf(k)) f |= 2u;
         if (!nonneg_finite(K)) f |= 4u;
-        const float ef = (float)e;
+        const float ef = unit_to_float(e);
         float inv_k = 0.0f, ka = 0.0f;
         if (!f) {
           if (kn0) {  // dynamic Kn: 1/k_i stored, k_a formed at every step
@@ -534,19 +668,25 @@ __global__ void __launch_bounds__(kMediumBX)
             ka = kf * fc_medium(Kf * kn_scale_max, kn_model);     // at the lowest pressure
             kn_out = Kf;
           } else {
-            const double inv = inv_ka(k, K, kn_model);            // Eq. 3 with Eq. 6-7 or 4-5
-            if (!(inv <= 1e15)) f |= 8u;                          // k_a >= 1e-15 (FP32 math)
-            inv_k = (float)inv;                                   // 0 for an open pore
-            ka = 1.0f / inv_k;
+            inv_k = inv_ka_pair(k, K, kn_model);                 // Eq. 3 with Eq. 6-7 or 4-5
+            if (!(inv_k <= 1e15f)) f |= 8u;                       // k_a >= 1e-15 (FP32 math)
           }
         }
         flags |= f;
         out = make_float2(ef, inv_k);
-        se += e;
+        const unsigned long long eb = (unsigned long long)__double_as_longlong(e);
+        if (eb >= (963ull << 52) && eb <= 0x3ff0000000000000ull)  // 2^-60 <= e <= 1
+          se = f2_add(se, f2_from_double(e));
+        else
+          se_small += e;  // below 2^-60, -0, and values the flags reject
         ++nodes;
         if (!f && ef > 0.0f) {
-          if (inv_k > 0.0f) ka_max = fmaxf(ka_max, ka);  // largest finite k_a
-          else ++open;                                   // open pores (k_a = inf)
+          if (inv_k > 0.0f) {  // finite k_a
+            if (kn0) ka_max = fmaxf(ka_max, ka);
+            else inv_min = fminf(inv_min, inv_k);
+          } else {
+            ++open;  // open pores (k_a = inf)
+          }
         }
       }
       med[jp] = out;
@@ -554,13 +694,14 @@ __global__ void __launch_bounds__(kMediumBX)
     }
   }
   if (flags) atomicOr(bad, flags);
-  double v[kNQ] = {se, (double)nodes, (double)ka_max, (double)open, 0.0, 0.0};
+  // the correctly rounded 1 / x does not increase with x: the largest of the
+  // nodes' 1 / inv_k is 1 / (their smallest inv_k)
+  if (inv_min < INFINITY) ka_max = fmaxf(ka_max, 1.0f / inv_min);
+  double v[kNQ] = {(double)se.hi + (double)se.lo + se_small, (double)nodes, (double)ka_max,
+                   (double)open, 0.0, 0.0};
   block_reduce_store<kMediumBX>(v, partials, kMediumMaxMask);
 }
 
-// One block per row up to 8 resident blocks of 256 threads on each of 152
-// SMs; wider grids only add partials.
-constexpr int kMediumMaxBlocks = 8 * 152;
 int medium_blocks(int nx, int ny) {
   (void)nx;
   return ny < kMediumMaxBlocks ? ny : kMediumMaxBlocks;

@@ -50,6 +50,10 @@ struct StepArgs {
   float kn_beta;        // dynamic Kn: p / p0 = 1 + kn_beta (rho - rho0)
   const float *kn0;     // dynamic Kn: [ny][pitch] Kn at p0 (medium then holds 1/k_i);
                         // NULL for a static Kn (medium holds 1/k_a)
+  int rev = 0;          // walk the launch's rows (direct) or tiles (staged) from the end:
+                        // alternate steps then start where the previous one finished,
+                        // on lines it left in L2.  The order of the nodes' updates
+                        // changes nothing in their results.
 };
 
 // ------------------------------------------------ hardware approximations

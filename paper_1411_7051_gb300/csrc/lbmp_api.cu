@@ -163,9 +163,13 @@ lbmp_status run_macro(lbmp_ctx *c, lbmp::MacroOut o, bool reduce) {
   return LBMP_OK;
 }
 
-// One step kernel launch (the variant the context selected).
-cudaError_t launch_one(lbmp_ctx *c, const StepArgs &a, const void *fin, void *fout, int k,
+// One step kernel launch (the variant the context selected).  Steps that
+// read buffer 1 walk the lattice from the end, so each step starts on the
+// nodes the previous one wrote last.
+cudaError_t launch_one(lbmp_ctx *c, const StepArgs &a0, const void *fin, void *fout, int k,
                        cudaStream_t s) {
+  StepArgs a = a0;
+  a.rev = fin == c->buf[1];
   if (c->wide) return lbmp::launch_wide(c->sr, a, c->rows(), fin, fout, c->med, c->d_tctr, k, s);
   if (c->staged)
     return lbmp::launch_staged(c->p.storage, c->sr, a, c->rows(), fin, fout, c->med, c->d_tctr,

@@ -244,6 +244,69 @@ __device__ __noinline__ void staged_edge_pair(const typename S::T *__restrict__ 
     S::template st2<SR>(fout + i * a.plane + o, dA[i], dB[i], SR ? pair_bits(h, i) : 0u, 0u);
 }
 
+// The populations of pressure column xb from its interior neighbour's pulled
+// values dn and state sn (non-equilibrium extrapolation, as staged_pressure).
+__device__ __forceinline__ void column_from_neighbour(const StepArgs &a, const float dn[9],
+                                                      const NodeState &sn, float eps_n, int xb,
+                                                      float eps_b, float d[9]) {
+  const float drho_b = (xb == 0) ? a.drho_in : a.drho_out;
+  float eq_b[9], eq_n[9];
+  equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, eps_b, eq_b);
+  equilibrium_dev(sn.drho_s * a.inv_scale, sn.rho, sn.ux, sn.uy, eps_n, eq_n);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) d[i] = fmaf(a.scale, eq_b[i] - eq_n[i], dn[i]);
+}
+
+// The same update with both nodes in the lanes of the packed arithmetic,
+// and a pressure column taking its neighbour's pull and state from the pair
+// (the batched kernel, whose short rows make edge pairs frequent: 125 -> 132
+// GLUPS on 256 instances; in the single-lattice kernel, where they are a
+// few per row, the scalar form above was the faster one).
+template <class S, bool SR, class Cfg = StageCfg<S>>
+__device__ __noinline__ void staged_edge_pair_packed(const typename S::T *__restrict__ sp,
+                                                     const typename S::T *__restrict__ fin,
+                                                     typename S::T *__restrict__ fout,
+                                                     const float2 *__restrict__ med,
+                                                     const StepArgs a, int c, int x, int y,
+                                                     float4 m, uint32_t ts) {
+  const bool two = x + 1 < a.nx;
+  float dA[9], dB[9];
+  pull_staged<S, Cfg>(sp, fin, a, 0, c, x, y, dA);
+  if (two) {
+    pull_staged<S, Cfg>(sp, fin, a, 0, c + 1, x + 1, y, dB);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dB[i] = 0.0f;
+  }
+  if (a.pressure) {
+    // a column next to its neighbour in the same pair takes the neighbour's
+    // pull and state from here; a lone last node of an odd row pulls its
+    // neighbour from the stage
+    if (x == 0)
+      column_from_neighbour(a, dB, node_state(dB, m.z, m.w, a), m.z, 0, m.x, dA);
+    else if (x == a.nx - 1)
+      staged_pressure<S, Cfg>(sp, fin, med, a, c - 1, x, y, m.x, dA);
+    if (two && x + 1 == a.nx - 1)
+      column_from_neighbour(a, dA, node_state(dA, m.x, m.y, a), m.x, a.nx - 1, m.z, dB);
+  }
+  // both nodes in the two lanes of the packed arithmetic (each lane gives the
+  // one-node bits); a lone last node of an odd row is stored as a pair with
+  // a zero in the row padding (x = nx < pitch, medium zero there), drawing
+  // its rounding bits as a pair
+  float2 d[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) d[i] = make_float2(dA[i], dB[i]);
+  const NodeStateT<float2> n = node_state_t<float2>(d, make_float2(m.x, m.z),
+                                                    make_float2(m.y, m.w), a);
+  collide_t<S::kHiLo>(d, n, a);
+  const long long o = (long long)y * a.pitch + x;
+  const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    S::template st2<SR>(fout + i * a.plane + o, d[i].x, two ? d[i].y : 0.0f,
+                        SR ? pair_bits(h, i) : 0u, 0u);
+}
+
 // Update of an interior node pair (2 <= x, x + 2 < nx, no plate
 // neighbour) at tile position c: every source is in the stage.  The pair is
 // computed in the two lanes of float2 values (packed FP32 arithmetic); each
@@ -305,7 +368,7 @@ __device__ __forceinline__ void staged_column_edges(const typename S::T *__restr
   const long long c = (long long)r * a.pitch + x - xT;  // position in the tile
   if (c < 0 || c >= Cfg::W) return;
   const float4 m = *reinterpret_cast<const float4 *>(sm + c);
-  staged_edge_pair<S, SR, Cfg>(sp, fin, fout, med, a, (int)c, x, y, m, ts);
+  staged_edge_pair_packed<S, SR, Cfg>(sp, fin, fout, med, a, (int)c, x, y, m, ts);
 }
 
 // ------------------------------------------------------------------ kernel
@@ -351,6 +414,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int tt = a.rev ? ntiles - 1 - t : t;  // the tile copied
       const int s = it % NS;
       const uint32_t use = (uint32_t)(it / NS);
       if (use > 0) {
@@ -364,11 +428,11 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
             mbar_wait(full((it - j) % NS), (uint32_t)((it - j) / NS) & 1u, err);
         return;
       }
-      const long long T0 = F0 + (long long)t * W;
+      const long long T0 = F0 + (long long)tt * W;
       const uint32_t med_bytes = (uint32_t)(min((long long)W, Fend - T0) * 8);
       if (lane == 0) mbar_arrive_expect_tx(full(s), 9u * kPlaneBytes + med_bytes);
       __syncwarp();
-      if (t == a.test_drop_tile) continue;  // the consumers' wait must run out
+      if (tt == a.test_drop_tile) continue;  // the consumers' wait must run out
       const uint32_t st = sbase + (uint32_t)L::kBarBytes + (uint32_t)s * (uint32_t)L::kStageBytes;
       if (lane < 9) {
         const int ey = (lane == 2 || lane == 5 || lane == 6) ? 1
@@ -402,7 +466,9 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   // Each consumer thread owns node pairs (x0, x0 + 1), x0 even, of the tile.
   constexpr int kPairs = (H * W / 2) / (kConsumerWarps * 32);
   // first node of this block's first tile, and the step between its tiles
-  const long long Tb = F0 + (long long)blockIdx.x * W;
+  // (backwards when the launch walks the tiles from the end)
+  const int t0 = a.rev ? ntiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
+  const long long Tb = F0 + (long long)t0 * W;
   int yT = (int)(Tb / a.pitch), xT = (int)(Tb - (long long)yT * a.pitch);
   const long long D = (long long)gridDim.x * W;
   const int dy = (int)(D / a.pitch), dx = (int)(D - (long long)dy * a.pitch);
@@ -432,11 +498,20 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty(s));
-    xT += dx;
-    yT += dy;
-    if (xT >= a.pitch) {
-      xT -= a.pitch;
-      ++yT;
+    if (a.rev) {
+      xT -= dx;
+      yT -= dy;
+      if (xT < 0) {
+        xT += a.pitch;
+        --yT;
+      }
+    } else {
+      xT += dx;
+      yT += dy;
+      if (xT >= a.pitch) {
+        xT -= a.pitch;
+        ++yT;
+      }
     }
   }
 }

@@ -129,6 +129,22 @@ def replay(nx, ny, walls, store, grids=(1, 7, 152), kind="single"):
                 if xT >= pitch:
                     xT -= pitch
                     yT += 1
+        # launches reading buffer 1 walk the tiles from the end: block b's
+        # k-th tile is ntiles - 1 - (b + k g), tracked backwards
+        seen = []
+        for b in range(g):
+            yT, xT = divmod(F0 + (ntiles - 1 - b) * W, pitch)
+            dy, dx = divmod(g * W, pitch)
+            for t in range(b, ntiles, g):
+                tt = ntiles - 1 - t
+                assert (yT, xT) == divmod(F0 + tt * W, pitch)
+                seen.append(tt)
+                xT -= dx
+                yT -= dy
+                if xT < 0:
+                    xT += pitch
+                    yT -= 1
+        assert sorted(seen) == list(range(ntiles))
     # the column-edge pass: consumer thread k takes row yT + k // 2, pair x = 0
     # (k even) or x = (nx - 1) & ~1 (k odd); with the consumer loop, which
     # skips those pairs, every pair of every tile is updated exactly once
