@@ -127,3 +127,37 @@ def test_pinned_host_inputs_match_pageable_ones():
         with pytest.raises(lbmp.LbmpError) as ei:
             b.set_fields(bad, pinned[1], pinned[2])
         assert ei.value.status == lbmp.EINVAL
+
+
+@pytest.mark.parametrize("kn_model", [lbmp.KN_BKC, lbmp.KN_FIRST_ORDER])
+def test_apparent_permeability_at_the_range_edges(orc, kn_model):
+    """k_i and Kn at and around the edges of the FP32-pair evaluation
+    (k_i in [1e-16, 1e12], Kn 0 or in [1e-12, 1e6]; outside them the
+    precompute takes the FP64 fraction), one ulp either side of each edge,
+    and the extremes it accepts: the same 1.3e-7 bound on both sides."""
+    up, dn = (lambda v: np.nextafter(v, np.inf)), (lambda v: np.nextafter(v, 0.0))
+    ks = [1e-14, dn(1e-16) * 100, 1e-16 * 100, 1e-12, 1.0, dn(1e12), 1e12, up(1e12), 1e13,
+          1e15, 3.7e-9]
+    kns = [0.0, 1e-14, dn(1e-12), 1e-12, up(1e-12), 1e-7, 0.5, 1.0, 3e3, dn(1e6), 1e6,
+           up(1e6), 1e7, 1e9]
+    # k_i = 1e-16 itself would give k_a below the 1e-15 floor; the pair path's
+    # lower edge is crossed with Kn large enough that k_a stays above it
+    kk = np.array([[k for k in ks] for _ in kns])
+    nn = np.array([[n for _ in ks] for n in kns])
+    edge = np.array([dn(1e-16), 1e-16, up(1e-16)])
+    kk = np.vstack([kk, np.tile(edge, (1, len(ks)))[:, :len(ks)]])
+    nn = np.vstack([nn, np.full((1, len(ks)), 1e3)])
+    ny, nx = kk.shape
+    eps = np.full((ny, nx), 0.4)
+    fc = orc.fc if kn_model == lbmp.KN_BKC else orc.fc_first_order
+    ref = kk * np.vectorize(fc)(nn)
+    ok = ref >= 1e-15 * (1 + 1e-6)
+    kk[~ok] = 1.0   # below the floor the medium is rejected (tested elsewhere)
+    ref = kk * np.vectorize(fc)(nn)
+    cfg = lbmp.SimConfig(nx, ny, kn_model=kn_model)
+    with lbmp.Sim(cfg) as sim:
+        sim.set_fields(eps, kk, nn)
+        ka = sim.apparent_permeability(device=False).numpy()
+    err = np.abs(ka / ref - 1.0)
+    _log(max_rel=float(err.max()), kn_model=kn_model)
+    assert err.max() <= REL, (err.max(), kk.flat[np.argmax(err)], nn.flat[np.argmax(err)])
