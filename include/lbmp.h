@@ -141,6 +141,10 @@ lbmp_status lbmp_destroy(lbmp_ctx *ctx);
  * (open pore); kn: Knudsen number >= 0, finite.  All [ny][nx] float64.
  * Stores per node eps and 1 / k_a with k_a = k_i f_c(Kn) (Eq. 3, 6-7), and
  * sets every population to w_i rho0.  Values of wall rows are ignored.
+ * 1 / k_a is formed in FP32-pair arithmetic (~44 significant bits; Kn^-0.4348
+ * from the hardware base-2 logarithm and power) and rounded to FP32: within
+ * ~1 FP32 ulp of Eq. 3.  Host arrays in pinned, device-mapped memory are read
+ * in place; other host memory is copied first.
  * Errors: EINVAL (a value out of range, or k_a < 1e-15; the context then
  * holds no valid medium until the next successful call), ECUDA. */
 lbmp_status lbmp_set_fields(lbmp_ctx *ctx, const double *eps, const double *k_i,
@@ -162,7 +166,7 @@ lbmp_status lbmp_macroscopic(lbmp_ctx *ctx, double *rho, double *ux, double *uy,
 
 /* Apparent permeability k_a = k_i f_c(Kn) (Eq. 3 with Eq. 6-7, or Eq. 4-5)
  * of every node as the step uses it: the reciprocal of the FP32 1/k_a that
- * lbmp_set_fields stored (f_c evaluated in FP32), [ny][nx] float64; +inf
+ * lbmp_set_fields stored, [ny][nx] float64; +inf
  * for an open pore, whatever the porosity of the node.  With a dynamic Kn,
  * k_a at the reference pressure p0 (the step's FP32 f_c of the Kn given).
  * Plate rows read 0.  Synchronous.  Errors: EINVAL, ESTATE (no fields
