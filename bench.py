@@ -414,10 +414,12 @@ def run_ours(args, ws, rank, local):
         res_other = time_storage(lbmp, torch, med, cfg, other, K, W, args.kernel,
                                  args.fp16_rounding)
     e2e = None if args.no_e2e else time_e2e(lbmp, torch, med, cfg, K)
-    dyn = None
+    dyn = dyn16 = None
     if not args.no_dynamic:
         dyn = time_storage(lbmp, torch, med, cfg, "fp32", K, W, "auto",
                            kn_beta=kn_beta_for(cfg))
+        dyn16 = time_storage(lbmp, torch, med, cfg, "fp16", K, W, "auto", args.fp16_rounding,
+                             kn_beta=kn_beta_for(cfg))
     adj = None if args.no_adjoint else adjoint_time(lbmp, torch, args.adjoint_steps)
     batch = None if args.no_batch else batch_object(lbmp, torch, args)
 
@@ -479,7 +481,7 @@ def run_ours(args, ws, rank, local):
     if dyn:
         g3 = ws * dyn["nodes"] * K / (dyn["ms"] * 1e-3) / 1e9
         r = roofline(dyn, "StoreF32")
-        r["traffic"] = r["traffic_per_update"] = None   # recorded for the static kernel only
+        r["traffic"] = r["traffic_per_update"] = r["achieved_dram"] = None  # static kernel only
         r["kernel"] = "lbmp::step_kernel<StoreF32, false, true> (dynamic Kn)"
         line["fp32_dynamic_kn"] = {
             "value": g3, "unit": "GLUPS", "ms_per_step": dyn["ms"] / K,
@@ -488,6 +490,17 @@ def run_ours(args, ws, rank, local):
                     "pressure twice the outlet one; the medium's Kn taken at p0), f_c of "
                     "Eq. 6-7 in FP32 at every step",
             "ratio_to_static": g3 / glups, "roofline": r, "k_g": dyn["k_g"]}
+    if dyn and dyn16:
+        g4 = ws * dyn16["nodes"] * K / (dyn16["ms"] * 1e-3) / 1e9
+        r = roofline(dyn16, "StoreF16")
+        r["traffic"] = r["traffic_per_update"] = r["achieved_dram"] = None
+        r["kernel"] = "lbmp::staged_step_kernel<StoreF16, SR, true> (dynamic Kn)"
+        line["fp16_dynamic_kn"] = {
+            "value": g4, "unit": "GLUPS", "ms_per_step": dyn16["ms"] / K,
+            "what": "the FP32 dynamic-Kn object with FP16-stored populations (48 B per "
+                    "update: the Kn plane at p0 staged beside the medium)",
+            "ratio_fp16_over_fp32": g4 / (ws * dyn["nodes"] * K / (dyn["ms"] * 1e-3) / 1e9),
+            "roofline": r, "fp16_scale": dyn16["scale"], "k_g": dyn16["k_g"]}
     if adj:
         line["adjoint"] = adjoint_object(adj, peak, peak_kind)
     if batch:

@@ -102,8 +102,9 @@ typedef struct lbmp_params {
                            p = p0 (1 + kn_beta (rho - rho0)) with rho its density
                            at the time level, its Kn = Kn(p0) p0 / p (the mean
                            free path of Eq. 10 is inversely proportional to p)
-                           and k_a = k_i f_c(Kn) is formed at every step.  Needs
-                           the direct kernel (AUTO picks it); 1 + kn_beta
+                           and k_a = k_i f_c(Kn) is formed at every step.
+                           FP32 storage needs the direct kernel, FP16 runs the
+                           staged one (AUTO) or the direct one; 1 + kn_beta
                            (rho - rho0) must stay > 0 (checked for rho_in and
                            rho_out), else velocities turn non-finite (ENAN).
                            Not available to lbmp_batch_* and the adjoint. */

@@ -153,11 +153,13 @@ template <>
 struct BatchCfg<StoreF32> {
   static constexpr int W = 1536, H = 1, A = 4, STAGES = 3;
   static constexpr int WARPS = 12;
+  static constexpr bool KN0 = false;  // batches have a static Kn
 };
 template <>
 struct BatchCfg<StoreF16> {
   static constexpr int W = 2304, H = 1, A = 8, STAGES = 3;
   static constexpr int WARPS = 12;
+  static constexpr bool KN0 = false;
 };
 template <class S>
 constexpr int batch_threads() {

@@ -149,43 +149,54 @@ cudaError_t launch_wide(bool sr, const StepArgs &a, int rows, const void *fin, v
 }
 
 // ------------------------------------------------------ staged variant
-template <class S, bool SR>
+template <class S, bool SR, bool DYN>
 static cudaError_t launch_staged_t(const StepArgs &a, int rows, const void *fin, void *fout,
                                    const float2 *med, const unsigned long long *tctr, int k,
                                    unsigned *err, int nsm, cudaStream_t s) {
-  using C = StageCfg<S>;
-  using L = StageLayout<S>;
+  using C = StageCfgFor<S, DYN>;
+  using L = StageLayout<S, C>;
   const long long span = (long long)rows * a.pitch;  // flat nodes of the launch rows
   const int ntiles = (int)((span + C::W - 1) / C::W);
   const int grid = ntiles < nsm ? ntiles : nsm;
-  staged_step_kernel<S, SR><<<grid, kStagedThreads, L::kSmemBytes, s>>>(
+  staged_step_kernel<S, SR, DYN><<<grid, kStagedThreads, L::kSmemBytes, s>>>(
       a, (const typename S::T *)fin, (typename S::T *)fout, med, tctr, k, rows, err);
   return cudaGetLastError();
 }
 
-cudaError_t prepare_staged() {
-  cudaError_t e;
-  e = cudaFuncSetAttribute(staged_step_kernel<StoreF32, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           StageLayout<StoreF32>::kSmemBytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(staged_step_kernel<StoreF16, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           StageLayout<StoreF16>::kSmemBytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(staged_step_kernel<StoreF16, true>,
+template <class S, bool SR, bool DYN>
+static cudaError_t staged_smem_attr() {
+  return cudaFuncSetAttribute(staged_step_kernel<S, SR, DYN>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              StageLayout<StoreF16>::kSmemBytes);
+                              StageLayout<S, StageCfgFor<S, DYN>>::kSmemBytes);
 }
 
+cudaError_t prepare_staged() {
+  cudaError_t e;
+  if ((e = staged_smem_attr<StoreF32, false, false>()) != cudaSuccess) return e;
+  if ((e = staged_smem_attr<StoreF16, false, false>()) != cudaSuccess) return e;
+  if ((e = staged_smem_attr<StoreF16, true, false>()) != cudaSuccess) return e;
+  if ((e = staged_smem_attr<StoreF16, false, true>()) != cudaSuccess) return e;
+  return staged_smem_attr<StoreF16, true, true>();
+}
+
+// A dynamic Kn (a.kn0 set) takes the FP16 kernel that also stages the Kn
+// plane; with FP32 storage the direct kernel serves it (the context never
+// selects the staged one).
 cudaError_t launch_staged(int storage, bool sr, const StepArgs &a, int rows, const void *fin,
                           void *fout, const float2 *med, const unsigned long long *tctr, int k,
                           unsigned *err, int nsm, cudaStream_t s) {
   if (rows <= 0 || a.nx <= 0) return cudaSuccess;
-  if (storage == 0)
-    return launch_staged_t<StoreF32, false>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
-  if (sr) return launch_staged_t<StoreF16, true>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
-  return launch_staged_t<StoreF16, false>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
+  const bool dyn = a.kn0 != nullptr;
+  if (storage == 0) {
+    if (dyn) return cudaErrorInvalidValue;
+    return launch_staged_t<StoreF32, false, false>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
+  }
+  if (dyn) {
+    if (sr) return launch_staged_t<StoreF16, true, true>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
+    return launch_staged_t<StoreF16, false, true>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
+  }
+  if (sr) return launch_staged_t<StoreF16, true, false>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
+  return launch_staged_t<StoreF16, false, false>(a, rows, fin, fout, med, tctr, k, err, nsm, s);
 }
 
 cudaError_t launch_bump(unsigned long long *tctr, int n, cudaStream_t s) {

@@ -305,13 +305,24 @@ __device__ __forceinline__ void solid_state(NodeStateT<V> &s, V c) {
   s.Fy = vmul(s.rFy, c);
 }
 
+// 1/k_a of a node with a dynamic Kn: inv_k is 1/k_i, kn0 the node's Kn at
+// p0, drho_s its (rho - rho0) S; p / p0 = 1 + kn_beta (rho - rho0) and
+// k_a = k_i f_c(kn0 p0 / p) (Eq. 3).  One node; the pair path applies it
+// lane by lane, so both give the same bits.
+__device__ __forceinline__ float dynamic_inv_k(float inv_k, float drho_s, float kn0,
+                                               const StepArgs &a) {
+  const float q = fmaf(a.kn_beta, __fmul_rn(drho_s, a.inv_scale), 1.0f);
+  return inv_k / fc_f32(kn0 / q, a.kn_model);
+}
+
 // Moments of Eq. 16a and the state of a node (one node, or a pair of nodes
-// in the lanes of V).  DYN (one node only): inv_k is 1/k_i and kn0 the
-// node's Kn at p0; its apparent permeability k_a = k_i f_c(kn0 p0 / p)
-// (Eq. 3) follows the pressure p / p0 = 1 + kn_beta (rho - rho0).
+// in the lanes of V).  DYN: inv_k is 1/k_i and kn0 the node's Kn at p0; its
+// apparent permeability k_a = k_i f_c(kn0 p0 / p) (Eq. 3) follows the
+// pressure p / p0 = 1 + kn_beta (rho - rho0).
 template <class V, bool DYN = false>
 __device__ __forceinline__ NodeStateT<V> node_state_t(const V d[9], V eps, V inv_k,
-                                                      const StepArgs &a, float kn0 = 0.0f) {
+                                                      const StepArgs &a,
+                                                      V kn0 = vsplat<V>(0.0f)) {
   NodeStateT<V> s;
   s.drho_s = vadd(vadd(vadd(d[0], vadd(d[1], d[3])), vadd(d[2], d[4])),
                   vadd(vadd(d[5], d[7]), vadd(d[6], d[8])));
@@ -323,16 +334,16 @@ __device__ __forceinline__ NodeStateT<V> node_state_t(const V d[9], V eps, V inv
   const V c = vmul(vsplat<V>(a.inv_scale), vrcp(s.rho));  // 1 / (S rho)
   if constexpr (sizeof(V) == sizeof(float)) {
     if (eps > 0.0f) {
-      if (DYN) {
-        const float q = fmaf(a.kn_beta, s.drho_s * a.inv_scale, 1.0f);
-        inv_k = inv_k / fc_f32(kn0 / q, a.kn_model);
-      }
+      if (DYN) inv_k = dynamic_inv_k(inv_k, s.drho_s, kn0, a);
       porous_state(s, eps, inv_k, c, a);
     } else {
       solid_state(s, c);
     }
   } else {
-    static_assert(!DYN, "the pair path has a static Kn");
+    if (DYN) {  // a solid lane's value is computed and not used
+      inv_k.x = dynamic_inv_k(inv_k.x, s.drho_s.x, kn0.x, a);
+      inv_k.y = dynamic_inv_k(inv_k.y, s.drho_s.y, kn0.y, a);
+    }
     const bool px = eps.x > 0.0f, py = eps.y > 0.0f;
     if (px && py) {  // the common case: two permeable nodes
       porous_state(s, eps, inv_k, c, a);

@@ -263,8 +263,9 @@ lbmp_status lbmp::validate_params(lbmp_params *p) {
       return fail(LBMP_EINVAL, "kn_model must be LBMP_KN_BKC or LBMP_KN_FIRST_ORDER");
     if (!std::isfinite(p->kn_beta)) return fail(LBMP_EINVAL, "kn_beta must be finite");
     if (p->kn_beta != 0.0) {
-      if (p->kernel == LBMP_KERNEL_STAGED)
-        return fail(LBMP_EINVAL, "a dynamic Kn (kn_beta != 0) needs the direct kernel");
+      if (p->kernel == LBMP_KERNEL_STAGED && p->storage != LBMP_STORE_FP16)
+        return fail(LBMP_EINVAL,
+                    "a dynamic Kn (kn_beta != 0) with FP32 storage needs the direct kernel");
       if (p->bc_x == LBMP_BCX_PRESSURE &&
           !(1.0 + p->kn_beta * (p->rho_in - p->rho0) > 0.0 &&
             1.0 + p->kn_beta * (p->rho_out - p->rho0) > 0.0))
@@ -357,10 +358,10 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
     c->elem = (p.storage == LBMP_STORE_FP32) ? 4 : 2;
     c->sr = p.storage == LBMP_STORE_FP16 && p.fp16_rounding == LBMP_ROUND_STOCHASTIC;
     // FP32: the direct kernel already saturates HBM (the staged one reaches
-    // ~0.95 of it); FP16: the staged kernel issues fewer instructions per node.
+    // ~0.95 of it); FP16 (static or dynamic Kn): the staged kernel issues
+    // fewer instructions per node.
     c->staged = p.kernel == LBMP_KERNEL_STAGED ||
-                (p.kernel == LBMP_KERNEL_AUTO && p.storage == LBMP_STORE_FP16 &&
-                 p.kn_beta == 0.0);
+                (p.kernel == LBMP_KERNEL_AUTO && p.storage == LBMP_STORE_FP16);
     c->wide = p.kernel == LBMP_KERNEL_WIDE;
     e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {

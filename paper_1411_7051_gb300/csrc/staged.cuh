@@ -27,6 +27,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lattice.cuh"
 
 namespace lbmp {
@@ -41,12 +43,23 @@ template <>
 struct StageCfg<StoreF32> {
   static constexpr int W = 1024, H = 1, A = 4, STAGES = 4;
   static constexpr int WARPS = kConsumerWarps;
+  static constexpr bool KN0 = false;
 };
 template <>
 struct StageCfg<StoreF16> {
   static constexpr int W = 2048, H = 1, A = 8, STAGES = 4;
   static constexpr int WARPS = kConsumerWarps;
+  static constexpr bool KN0 = false;
 };
+// FP16 with a dynamic Kn: each stage also holds the tile's Kn at p0 (a
+// float per node), so the ring is one stage shorter.
+struct StageCfgDyn16 {
+  static constexpr int W = 2048, H = 1, A = 8, STAGES = 3;
+  static constexpr int WARPS = kConsumerWarps;
+  static constexpr bool KN0 = true;
+};
+template <class S, bool DYN>
+using StageCfgFor = typename std::conditional<DYN, StageCfgDyn16, StageCfg<S>>::type;
 
 // Shared-memory layout of a stage configuration Cfg (tile width W, halo A,
 // STAGES, WARPS consumer warps).
@@ -57,10 +70,12 @@ struct StageLayout {
   static constexpr int RW = C::W + 2 * C::A;  // stage row length (elements)
   static constexpr int kPopBytes = 9 * C::H * RW * (int)sizeof(T);
   static constexpr int kMedBytes = C::H * C::W * 8;
-  static constexpr int kStageBytes = kPopBytes + kMedBytes;
+  static constexpr int kKnBytes = C::KN0 ? C::H * C::W * 4 : 0;  // Kn at p0 (dynamic Kn)
+  static constexpr int kStageBytes = kPopBytes + kMedBytes + kKnBytes;
   static constexpr int kBarBytes = 128;  // full[STAGES], empty[STAGES]
   static constexpr int kSmemBytes = kBarBytes + C::STAGES * kStageBytes;
-  static_assert(kPopBytes % 16 == 0 && kMedBytes % 16 == 0, "16-byte stage alignment");
+  static_assert(kPopBytes % 16 == 0 && kMedBytes % 16 == 0 && kKnBytes % 16 == 0,
+                "16-byte stage alignment");
   static_assert(RW * (int)sizeof(T) % 16 == 0, "16-byte row alignment");
   static_assert(C::A * (int)sizeof(T) == 16, "halo of 16 bytes");
   static_assert(2 * C::STAGES * 8 <= kBarBytes, "barrier area");
@@ -187,16 +202,17 @@ __device__ __forceinline__ uint32_t pair_bits(uint32_t h, int i) {
 
 // Pressure column xb (0 or nx - 1) at tile position c: non-equilibrium
 // extrapolation from the neighbouring interior node (stage position cn).
-template <class S, class Cfg = StageCfg<S>>
+template <class S, class Cfg = StageCfg<S>, bool DYN = false>
 __device__ __forceinline__ void staged_pressure(const typename S::T *__restrict__ sp,
                                                 const typename S::T *__restrict__ fin,
                                                 const float2 *__restrict__ med, const StepArgs &a,
                                                 int cn, int xb, int y, float eps_b, float d[9]) {
   const int xn = (xb == 0) ? 1 : a.nx - 2;
-  const float2 mn = med[(long long)y * a.pitch + xn];
+  const long long jn = (long long)y * a.pitch + xn;
+  const float2 mn = med[jn];
   float dn[9];
   pull_staged<S, Cfg>(sp, fin, a, 0, cn, xn, y, dn);
-  const NodeState sn = node_state(dn, mn.x, mn.y, a);
+  const NodeState sn = node_state<DYN>(dn, mn.x, mn.y, a, DYN ? a.kn0[jn] : 0.0f);
   const float drho_b = (xb == 0) ? a.drho_in : a.drho_out;
   float eq_b[9], eq_n[9];
   equilibrium_dev(drho_b, a.rho0 + drho_b, sn.ux, sn.uy, eps_b, eq_b);
@@ -211,25 +227,27 @@ __device__ __forceinline__ void staged_pressure(const typename S::T *__restrict_
 // row; keeping them out of line keeps the interior path's registers and
 // code lean.  The step arguments come by value: taking the address of the
 // kernel parameter would move every read of it to local memory.
-template <class S, bool SR, class Cfg = StageCfg<S>>
+template <class S, bool SR, class Cfg = StageCfg<S>, bool DYN = false>
 __device__ __noinline__ void staged_edge_pair(const typename S::T *__restrict__ sp,
                                               const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout,
                                               const float2 *__restrict__ med, const StepArgs a,
-                                              int c, int x, int y, float4 m, uint32_t ts) {
+                                              int c, int x, int y, float4 m, float2 k0,
+                                              uint32_t ts) {
   const bool two = x + 1 < a.nx;
   float dA[9], dB[9];
   pull_staged<S, Cfg>(sp, fin, a, 0, c, x, y, dA);
   if (two) pull_staged<S, Cfg>(sp, fin, a, 0, c + 1, x + 1, y, dB);
   if (a.pressure) {
     if (x == 0 || x == a.nx - 1)
-      staged_pressure<S, Cfg>(sp, fin, med, a, x == 0 ? c + 1 : c - 1, x, y, m.x, dA);
-    if (two && x + 1 == a.nx - 1) staged_pressure<S, Cfg>(sp, fin, med, a, c, x + 1, y, m.z, dB);
+      staged_pressure<S, Cfg, DYN>(sp, fin, med, a, x == 0 ? c + 1 : c - 1, x, y, m.x, dA);
+    if (two && x + 1 == a.nx - 1)
+      staged_pressure<S, Cfg, DYN>(sp, fin, med, a, c, x + 1, y, m.z, dB);
   }
-  const NodeState nA = node_state(dA, m.x, m.y, a);
+  const NodeState nA = node_state<DYN>(dA, m.x, m.y, a, k0.x);
   collide<S::kHiLo>(dA, nA, a);
   if (two) {
-    const NodeState nB = node_state(dB, m.z, m.w, a);
+    const NodeState nB = node_state<DYN>(dB, m.z, m.w, a, k0.y);
     collide<S::kHiLo>(dB, nB, a);
   } else {
     // a last node of an odd row is stored as a pair with a zero in the row
@@ -311,11 +329,12 @@ __device__ __noinline__ void staged_edge_pair_packed(const typename S::T *__rest
 // neighbour) at tile position c: every source is in the stage.  The pair is
 // computed in the two lanes of float2 values (packed FP32 arithmetic); each
 // lane gives the bits of the one-node update.
-template <class S, bool SR, class Cfg = StageCfg<S>>
+template <class S, bool SR, class Cfg = StageCfg<S>, bool DYN = false>
 __device__ __forceinline__ void staged_interior_pair(const typename S::T *__restrict__ sp,
                                                      typename S::T *__restrict__ fout,
                                                      const StepArgs &a, int c, int x, int y,
-                                                     float4 m, uint32_t ts) {
+                                                     float4 m, uint32_t ts,
+                                                     float2 k0 = make_float2(0.0f, 0.0f)) {
   using L = StageLayout<S, Cfg>;
   constexpr int PL = L::RW;  // elements between planes in a stage
   float2 d[9];               // lane x: node x, lane y: node x + 1
@@ -330,8 +349,8 @@ __device__ __forceinline__ void staged_interior_pair(const typename S::T *__rest
   d[3] = make_float2(S::ld1(row + 3 * PL + 1), S::ld1(row + 3 * PL + 2));
   d[6] = make_float2(S::ld1(row + 6 * PL + 1), S::ld1(row + 6 * PL + 2));
   d[7] = make_float2(S::ld1(row + 7 * PL + 1), S::ld1(row + 7 * PL + 2));
-  const NodeStateT<float2> n = node_state_t<float2>(d, make_float2(m.x, m.z),
-                                                    make_float2(m.y, m.w), a);
+  const NodeStateT<float2> n = node_state_t<float2, DYN>(d, make_float2(m.x, m.z),
+                                                         make_float2(m.y, m.w), a, k0);
   collide_t<S::kHiLo>(d, n, a);
   const long long o = (long long)y * a.pitch + x;
   const uint32_t h = SR ? mix32((uint32_t)(o >> 1) ^ ts) : 0u;
@@ -372,14 +391,15 @@ __device__ __forceinline__ void staged_column_edges(const typename S::T *__restr
 }
 
 // ------------------------------------------------------------------ kernel
-template <class S, bool SR>
+template <class S, bool SR, bool DYN = false>
 __global__ void __launch_bounds__(kStagedThreads, 1)
     staged_step_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
                        typename S::T *__restrict__ fout, const float2 *__restrict__ med,
                        const unsigned long long *__restrict__ tctr, int k, int rows,
                        unsigned *err) {
-  using L = StageLayout<S>;
-  using C = StageCfg<S>;
+  using C = StageCfgFor<S, DYN>;
+  using L = StageLayout<S, C>;
+  static_assert(C::KN0 == DYN, "a dynamic Kn stages the Kn plane");
   using T = typename S::T;
   constexpr int W = C::W, H = C::H, A = C::A, NS = C::STAGES, RW = L::RW;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -409,7 +429,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   if (warp == kConsumerWarps) {
     // ------------------------------------------------------- producer
     // Lane i < 9 copies plane i (one or a few segments), lane 9 the medium,
-    // after lane 0 has posted the expected byte count.
+    // lane 10 (dynamic Kn) the Kn at p0, after lane 0 has posted the
+    // expected byte count.
     constexpr uint32_t kPlaneBytes = (uint32_t)(RW * sizeof(T));
     int it = 0;
     bool ok = true;
@@ -430,7 +451,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
       }
       const long long T0 = F0 + (long long)tt * W;
       const uint32_t med_bytes = (uint32_t)(min((long long)W, Fend - T0) * 8);
-      if (lane == 0) mbar_arrive_expect_tx(full(s), 9u * kPlaneBytes + med_bytes);
+      const uint32_t kn_bytes = DYN ? med_bytes / 2 : 0u;
+      if (lane == 0) mbar_arrive_expect_tx(full(s), 9u * kPlaneBytes + med_bytes + kn_bytes);
       __syncwarp();
       if (tt == a.test_drop_tile) continue;  // the consumers' wait must run out
       const uint32_t st = sbase + (uint32_t)L::kBarBytes + (uint32_t)s * (uint32_t)L::kStageBytes;
@@ -452,6 +474,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
         }
       } else if (lane == 9) {
         bulk_g2s(st + (uint32_t)L::kPopBytes, med + T0, med_bytes, full(s));
+      } else if (DYN && lane == 10) {
+        bulk_g2s(st + (uint32_t)(L::kPopBytes + L::kMedBytes), a.kn0 + T0, kn_bytes, full(s));
       }
     }
     return;
@@ -479,6 +503,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const unsigned char *sb = smem + L::kBarBytes + s * L::kStageBytes;
     const T *sp = reinterpret_cast<const T *>(sb);
     const float2 *sm = reinterpret_cast<const float2 *>(sb + L::kPopBytes);
+    const float *sk = reinterpret_cast<const float *>(sb + L::kPopBytes + L::kMedBytes);
 #pragma unroll 1
     for (int j = 0; j < kPairs; ++j) {
       const int q = threadIdx.x + j * kConsumerWarps * 32;  // pair index in the tile
@@ -490,11 +515,12 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
       }
       if (y >= y_end || x >= a.nx) continue;
       const float4 m = *reinterpret_cast<const float4 *>(sm + c);
+      const float2 k0 = DYN ? *reinterpret_cast<const float2 *>(sk + c) : make_float2(0.0f, 0.0f);
       if (x == 0 || x + 2 >= a.nx || (a.walls && (y == 1 || y == a.ny - 2))) {
-        staged_edge_pair<S, SR>(sp, fin, fout, med, a, c, x, y, m, ts);
+        staged_edge_pair<S, SR, C, DYN>(sp, fin, fout, med, a, c, x, y, m, k0, ts);
         continue;
       }
-      staged_interior_pair<S, SR>(sp, fout, a, c, x, y, m, ts);
+      staged_interior_pair<S, SR, C, DYN>(sp, fout, a, c, x, y, m, ts, k0);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty(s));

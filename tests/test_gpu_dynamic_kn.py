@@ -185,7 +185,7 @@ def test_unsupported_combinations():
             s.permeability_gradient(10)
         assert e.value.status == lbmp.EINVAL
         assert s.info().bytes_per_update == 84.0
-    # FP16 + dynamic Kn runs the direct kernel
+    # FP16 + dynamic Kn runs the staged kernel with the Kn plane staged
     with gpu_sim(case, FP16) as s:
         s.step(10)
         assert np.isfinite(s.permeability()[0])

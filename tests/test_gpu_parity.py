@@ -316,6 +316,28 @@ def test_staged_matches_direct(storage, walls, pressure):
     assert ka == kb
 
 
+@pytest.mark.parametrize("walls,pressure", [(True, True), (False, False)])
+def test_staged_matches_direct_dynamic_kn(walls, pressure):
+    """FP16 with a dynamic Kn: the staged kernel (which stages the Kn plane
+    beside the medium) and the direct kernel form f_c(Kn0 p0 / p) node by
+    node with the same operations, so the populations agree bit for bit
+    (round-to-nearest)."""
+    med = media.random_medium(300, 41, seed=14, p_open=0.1, p_solid=0.1, log10_k_range=(-3, 0),
+                              kn_range=(0.0, 5.0))
+    case = Case(300, 41, tau=0.7, G=(1e-5, 0.0), walls=walls, pressure=pressure,
+                rho_in=1.001, rho_out=0.999, forchheimer=1, medium=med, kn_beta=100.0)
+    a = gpu_sim(case, FP16, kernel=STAGED, fp16_rounding=RN)
+    b = gpu_sim(case, FP16, kernel=DIRECT, fp16_rounding=RN)
+    assert a.info().bytes_per_update == b.info().bytes_per_update == 48.0
+    a.step(50)
+    b.step(50)
+    fa, fb = _np(a.populations()), _np(b.populations())
+    assert np.array_equal(fa, fb), f"{np.sum(fa != fb)} populations differ"
+    ka, _ = a.permeability()
+    kb, _ = b.permeability()
+    assert ka == kb
+
+
 def test_bounded_wait_reports_timeout(monkeypatch):
     """The staged kernel's waits are bounded: with the copies of one tile
     withheld, the consumers give up after their limit, the host reports

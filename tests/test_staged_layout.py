@@ -28,7 +28,13 @@ def stage_cfg(kind="single"):
                       r"A = (\d+), STAGES = (\d+);" % store, text)
         assert m, store
         W, H, A, NS = map(int, m.groups())
-        out[store] = dict(W=W, H=H, A=A, NS=NS, elem=elem, warps=cw, head=0)
+        out[store] = dict(W=W, H=H, A=A, NS=NS, elem=elem, warps=cw, head=0, kn0=False)
+    if kind == "dyn":  # FP16 with a dynamic Kn: the Kn plane staged too
+        m = re.search(r"struct StageCfgDyn16\s*{\s*static constexpr int W = (\d+), H = (\d+), "
+                      r"A = (\d+), STAGES = (\d+);", text)
+        assert m
+        W, H, A, NS = map(int, m.groups())
+        out = {"StoreF16": dict(W=W, H=H, A=A, NS=NS, elem=2, warps=cw, head=0, kn0=True)}
     if kind == "batch":
         btext = open(os.path.join(CSRC, "batch.cu")).read()
         head = int(re.search(r"kHeadBytes = (\d+);", btext).group(1))
@@ -38,7 +44,7 @@ def stage_cfg(kind="single"):
                           btext)
             assert m, store
             W, H, A, NS, warps = map(int, m.groups())
-            out[store] = dict(W=W, H=H, A=A, NS=NS, elem=elem, warps=warps, head=head)
+            out[store] = dict(W=W, H=H, A=A, NS=NS, elem=elem, warps=warps, head=head, kn0=False)
     return out
 
 
@@ -60,7 +66,7 @@ def replay(nx, ny, walls, store, grids=(1, 7, 152), kind="single"):
     assert H == 1 and W % 64 == 0
     RW = W + 2 * A
     pop_bytes = 9 * RW * elem
-    stage_bytes = pop_bytes + W * 8
+    stage_bytes = pop_bytes + W * 8 + (W * 4 if c["kn0"] else 0)
     bar_bytes = 128
     assert bar_bytes + NS * stage_bytes + NS * c["head"] <= 227 * 1024
     assert (bar_bytes + NS * stage_bytes) % 16 == 0  # the batched tile headers follow
@@ -75,8 +81,12 @@ def replay(nx, ny, walls, store, grids=(1, 7, 152), kind="single"):
         T0 = F0 + t * W
         assert T0 < Fend
         med_elems = min(W, Fend - T0)
-        total = 9 * RW * elem + med_elems * 8
+        total = 9 * RW * elem + med_elems * 8 + (med_elems * 4 if c["kn0"] else 0)
         assert total < 2 ** 20  # mbarrier tx-count range
+        if c["kn0"]:
+            # the Kn span [T0, T0 + med_elems) of the float plane, after the medium
+            assert (T0 * 4) % 16 == 0 and (med_elems * 4) % 16 == 0
+            assert (pop_bytes + W * 8) % 16 == 0
         for lane in range(9):
             # producer lane `lane`: plane lane's sources, flat [T0 - e_y pitch - A, + RW) mod NP
             v = T0 - EY[lane] * pitch - A
@@ -188,8 +198,10 @@ def replay(nx, ny, walls, store, grids=(1, 7, 152), kind="single"):
 @pytest.mark.parametrize("walls", [False, True])
 @pytest.mark.parametrize("nx,ny", [(1, 3), (3, 3), (5, 1), (64, 33), (131, 37), (255, 9), (256, 4),
                                    (257, 5), (513, 17), (1000, 7), (4096, 12), (4099, 6)])
-@pytest.mark.parametrize("kind", ["single", "batch"])
+@pytest.mark.parametrize("kind", ["single", "batch", "dyn"])
 def test_staged_copies_in_bounds_and_aligned(nx, ny, walls, store, kind):
     if walls and ny < 3:
         pytest.skip("walls need ny >= 3")
+    if kind == "dyn" and store != "StoreF16":
+        pytest.skip("a dynamic Kn stages FP16 populations only")
     replay(nx, ny, walls, store, kind=kind)
