@@ -463,16 +463,8 @@ cudaError_t launch_histogram(int storage, const StepArgs &a, const void *fin, co
 }
 
 // ---------------------------------------------------------------- medium
-// f_c of Eq. 6-7 (b = -1; model 0) or of Eq. 4-5 (model 1) in FP32, for the
-// largest k_a of a dynamic-Kn medium (it only sets the FP16 scale).  Kn = 0
-// gives 1: Kn^-0.4348 = inf, alpha = 0 and Kn / (1 + Kn) = 0.
-__device__ __forceinline__ float fc_medium(float kn, int model) {
-  if (model == 1) return fmaf(4.0f, kn, 1.0f);
-  const float t = exp2f(-0.4348f * log2f(kn));
-  const float alpha = 1.358f / fmaf(0.170f, t, 1.0f);
-  const float r = kn < 1e30f ? kn / (1.0f + kn) : 1.0f;  // no inf / inf at huge Kn
-  return fmaf(alpha, kn, 1.0f) * fmaf(4.0f, r, 1.0f);
-}
+// The largest k_a of a dynamic-Kn medium (it only sets the FP16 scale) takes
+// fc_f32 of the lattice header.
 
 // 1 / k_a = 1 / (k_i f_c(Kn)) of Eq. 3 in FP64 with a single division.
 // Eq. 6-7 (b = -1) as one fraction: with t = Kn^-0.4348 and a = 1 + 0.17 t,
@@ -549,24 +541,6 @@ __device__ __forceinline__ F2 f2_from_double(double d) {
   const float lo_int = (float)(unsigned)(b & 0x1fffffffull);  // the low 29 mantissa bits
   const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);  // 2^(e - 52)
   return {__uint_as_float(hib), (b >> 63) ? -lo_int * scale : lo_int * scale};
-}
-
-// Kn^-0.4348 for Kn in [1e-12, 1e6] from the hardware base-2 logarithm and
-// power (lg2.approx: absolute error ~2^-22.6, the exponent part exact;
-// ex2.approx: relative ~2^-22.5).  The exponent y = -0.4348 log2 Kn (|y| up
-// to 17) is carried as y_hi + y_lo (exact product, the constant as hi + lo)
-// and 2^y = 2^y_hi (1 + ln2 y_lo): ~3e-7 relative in all, where rounding y
-// to one FP32 would alone cost up to 7e-7.  t enters the fraction with a
-// sensitivity below 0.08.
-__device__ __forceinline__ float kn_power(float K) {
-  constexpr float c_hi = -0.4348f;
-  constexpr float c_lo = (float)(-0.4348 - (double)c_hi);
-  float lg, t;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(K));
-  const float y_hi = __fmul_rn(lg, c_hi);
-  const float y_lo = __fmaf_rn(lg, c_lo, __fmaf_rn(lg, c_hi, -y_hi));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(y_hi));
-  return __fmaf_rn(__fmul_rn(t, 0.69314718f), y_lo, t);
 }
 
 // 1 / k_a of inv_ka() for k_i and Kn in the ranges FP32 pairs hold
@@ -676,7 +650,7 @@ __global__ void __launch_bounds__(kMediumBX, kMediumMaxBlocks / 152)
             const float kf = (float)k, Kf = (float)K;
             if (!(kf >= 1e-15f)) f |= 8u;
             inv_k = 1.0f / kf;                                    // 0 for k_i = inf
-            ka = kf * fc_medium(Kf * kn_scale_max, kn_model);     // at the lowest pressure
+            ka = kf * fc_f32(Kf * kn_scale_max, kn_model);     // at the lowest pressure
             kn_out = Kf;
           } else {
             inv_k = inv_ka_pair(k, K, kn_model);                 // Eq. 3 with Eq. 6-7 or 4-5
@@ -742,7 +716,7 @@ __global__ void __launch_bounds__(kMediumBX)
   if (y >= y_lo && y < y_hi) {
     const long long jp = (long long)y * pitch + x;
     float inv = med[jp].y;
-    if (kn0) inv = inv / fc_f32(kn0[jp], kn_model);
+    if (kn0) inv = inv_ka_dynamic(inv, kn0[jp], kn_model);  // the step's form at p = p0
     v = 1.0 / (double)inv;  // inf for an open pore (1/k_a = 0)
   }
   ka[(long long)y * nx + x] = v;

@@ -82,14 +82,59 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   return h;
 }
 
-// f_c of Eq. 6-7 (b = -1; model 0) or of Eq. 4-5 (model 1) in FP32, for the
-// Knudsen number of a node at its current pressure (dynamic Kn).  At Kn = 0
-// the power Kn^-0.4348 is +inf, alpha 0 and f_c exactly 1.
+// f_c of Eq. 6-7 (b = -1; model 0) or of Eq. 4-5 (model 1) in FP32, any
+// Kn >= 0.  At Kn = 0 the power Kn^-0.4348 is +inf, alpha 0 and f_c exactly
+// 1; at huge Kn, Kn / (1 + Kn) is taken as 1 (no inf / inf).
 __device__ __forceinline__ float fc_f32(float kn, int model) {
   if (model == 1) return fmaf(4.0f, kn, 1.0f);
   const float t = exp2f(-0.4348f * log2f(kn));
   const float alpha = 1.358f / fmaf(0.170f, t, 1.0f);
-  return fmaf(alpha, kn, 1.0f) * (1.0f + 4.0f * kn / (1.0f + kn));
+  const float r = kn < 1e30f ? kn / (1.0f + kn) : 1.0f;
+  return fmaf(alpha, kn, 1.0f) * fmaf(4.0f, r, 1.0f);
+}
+
+// Kn^-0.4348 for a normal FP32 Kn from the hardware base-2 logarithm and
+// power (lg2.approx: absolute error ~2^-22.6, the exponent part exact;
+// ex2.approx: relative ~2^-22.5).  The exponent y = -0.4348 log2 Kn is
+// carried as y_hi + y_lo (exact product, the constant as hi + lo) and
+// 2^y = 2^y_hi (1 + ln2 y_lo): ~3e-7 relative in all, where rounding y to
+// one FP32 would alone cost up to 7e-7 at |y| ~ 17.  t enters f_c with a
+// sensitivity below 0.08.
+__device__ __forceinline__ float kn_power(float K) {
+  constexpr float c_hi = -0.4348f;
+  constexpr float c_lo = (float)(-0.4348 - (double)c_hi);
+  float lg, t;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(K));
+  const float y_hi = __fmul_rn(lg, c_hi);
+  const float y_lo = __fmaf_rn(lg, c_lo, __fmaf_rn(lg, c_hi, -y_hi));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(y_hi));
+  return __fmaf_rn(__fmul_rn(t, 0.69314718f), y_lo, t);
+}
+
+// n / d (d normal, positive) from the approximate reciprocal and one Newton
+// correction of the quotient: q0 = n r, q0 + r (n - d q0) with the residual
+// exact by fma; within ~1 ulp, where the IEEE division takes a longer
+// sequence.
+__device__ __forceinline__ float div_newton(float n, float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  const float q = __fmul_rn(n, r);
+  return __fmaf_rn(r, __fmaf_rn(-d, q, n), q);
+}
+
+// (1/k_i) / f_c(Kn) (Eq. 3) for a node's current Kn, as one fraction:
+// f_c = ((a + 1.358 Kn) / a) ((1 + 5 Kn) / (1 + Kn)) with a = 1 + 0.17
+// Kn^-0.4348 (Eq. 6-7, b = -1), so one division where the factor form
+// takes three; Eq. 4-5: (1/k_i) / (1 + 4 Kn).  Kn = 0 (and subnormal Kn)
+// gives f_c = 1; Kn above 1e12 takes fc_f32 (the fraction would overflow).
+__device__ __forceinline__ float inv_ka_dynamic(float inv_k, float kn, int model) {
+  if (model == 1) return div_newton(inv_k, __fmaf_rn(4.0f, kn, 1.0f));
+  if (!(kn >= 1.17549435e-38f)) return inv_k;
+  if (kn > 1e12f) return inv_k / fc_f32(kn, 0);
+  const float a = __fmaf_rn(0.17f, kn_power(kn), 1.0f);
+  const float num = __fmul_rn(__fmul_rn(inv_k, a), __fadd_rn(1.0f, kn));
+  const float den = __fmul_rn(__fmaf_rn(1.358f, kn, a), __fmaf_rn(5.0f, kn, 1.0f));
+  return div_newton(num, den);
 }
 
 // ----------------------------------------------------------------- storage
@@ -312,7 +357,7 @@ __device__ __forceinline__ void solid_state(NodeStateT<V> &s, V c) {
 __device__ __forceinline__ float dynamic_inv_k(float inv_k, float drho_s, float kn0,
                                                const StepArgs &a) {
   const float q = fmaf(a.kn_beta, __fmul_rn(drho_s, a.inv_scale), 1.0f);
-  return inv_k / fc_f32(kn0 / q, a.kn_model);
+  return inv_ka_dynamic(inv_k, div_newton(kn0, q), a.kn_model);
 }
 
 // Moments of Eq. 16a and the state of a node (one node, or a pair of nodes
