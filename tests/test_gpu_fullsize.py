@@ -76,7 +76,7 @@ def _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=0, kn_beta=0
 
 
 @pytest.mark.parametrize("storage,dynamic", [(lbmp.STORE_FP32, False), (lbmp.STORE_FP16, False),
-                                             (lbmp.STORE_FP32, True)])
+                                             (lbmp.STORE_FP32, True), (lbmp.STORE_FP16, True)])
 def test_bench_workload_sampled_step(orc, storage, dynamic):
     """The bench workload (4096^2 fractured shale, pressure x, periodic y,
     Forchheimer), AUTO kernel selection as timed by bench.py; also its

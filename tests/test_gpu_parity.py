@@ -338,20 +338,23 @@ def test_staged_matches_direct_dynamic_kn(walls, pressure):
     assert ka == kb
 
 
-def test_bounded_wait_reports_timeout(monkeypatch):
+@pytest.mark.parametrize("storage,kn_beta", [(FP32, 0.0), (FP16, 50.0)])
+def test_bounded_wait_reports_timeout(monkeypatch, storage, kn_beta):
     """The staged kernel's waits are bounded: with the copies of one tile
     withheld, the consumers give up after their limit, the host reports
-    ETIMEOUT, and the context stays usable."""
+    ETIMEOUT, and the context stays usable.  FP16 with a dynamic Kn runs the
+    form that also stages the Kn plane."""
     from paper_1411_7051_gb300 import lbmp
     monkeypatch.setenv("LBMP_TEST_DROP_TILE", "3")
     case = _two_component_case(n=1024, ny=64)
-    gs = gpu_sim(case, FP32, kernel=STAGED)
+    case.kn_beta = kn_beta
+    gs = gpu_sim(case, storage, kernel=STAGED)
     monkeypatch.delenv("LBMP_TEST_DROP_TILE")
     gs.step(1)
     with pytest.raises(lbmp.LbmpError) as ei:
         gs.synchronize()
     assert ei.value.status == lbmp.ETIMEOUT
-    ok = gpu_sim(case, FP32, kernel=STAGED)   # a fresh context works
+    ok = gpu_sim(case, storage, kernel=STAGED)   # a fresh context works
     ok.step(5)
     ok.synchronize()
 
