@@ -360,6 +360,50 @@ __device__ __forceinline__ float dynamic_inv_k(float inv_k, float drho_s, float 
   return inv_ka_dynamic(inv_k, div_newton(kn0, q), a.kn_model);
 }
 
+// The pair forms: the same operations in the two lanes of the packed
+// instructions (which round as the scalar ones; the negations as exact
+// products by -1), so each lane gives dynamic_inv_k's bits.
+__device__ __forceinline__ float2 rcp2(float2 d) {
+  float2 r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(d.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(d.y));
+  return r;
+}
+__device__ __forceinline__ float2 div_newton(float2 n, float2 d) {
+  const float2 r = rcp2(d);
+  const float2 q = vmul(n, r);
+  return vfma(r, vfma(vmul(vsplat<float2>(-1.0f), d), q, n), q);
+}
+__device__ __forceinline__ float2 kn_power(float2 K) {
+  constexpr float c_hi = -0.4348f;
+  constexpr float c_lo = (float)(-0.4348 - (double)c_hi);
+  float2 lg, t;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg.x) : "f"(K.x));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg.y) : "f"(K.y));
+  const float2 y_hi = vmul(lg, vsplat<float2>(c_hi));
+  const float2 y_lo = vfma(lg, vsplat<float2>(c_lo),
+                           vfma(lg, vsplat<float2>(c_hi), vmul(vsplat<float2>(-1.0f), y_hi)));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t.x) : "f"(y_hi.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t.y) : "f"(y_hi.y));
+  return vfma(vmul(t, vsplat<float2>(0.69314718f)), y_lo, t);
+}
+__device__ __forceinline__ float2 dynamic_inv_k(float2 inv_k, float2 drho_s, float2 kn0,
+                                                const StepArgs &a) {
+  const float2 q = vfma(vsplat<float2>(a.kn_beta), vmul(drho_s, vsplat<float2>(a.inv_scale)),
+                        vsplat<float2>(1.0f));
+  const float2 kn = div_newton(kn0, q);
+  const bool common = a.kn_model == 0 && kn.x >= 1.17549435e-38f && kn.x <= 1e12f &&
+                      kn.y >= 1.17549435e-38f && kn.y <= 1e12f;
+  if (!common)  // the one-node form, lane by lane
+    return make_float2(inv_ka_dynamic(inv_k.x, kn.x, a.kn_model),
+                       inv_ka_dynamic(inv_k.y, kn.y, a.kn_model));
+  const float2 one = vsplat<float2>(1.0f);
+  const float2 ca = vfma(vsplat<float2>(0.17f), kn_power(kn), one);
+  const float2 num = vmul(vmul(inv_k, ca), vadd(one, kn));
+  const float2 den = vmul(vfma(vsplat<float2>(1.358f), kn, ca), vfma(vsplat<float2>(5.0f), kn, one));
+  return div_newton(num, den);
+}
+
 // Moments of Eq. 16a and the state of a node (one node, or a pair of nodes
 // in the lanes of V).  DYN: inv_k is 1/k_i and kn0 the node's Kn at p0; its
 // apparent permeability k_a = k_i f_c(kn0 p0 / p) (Eq. 3) follows the
@@ -385,10 +429,7 @@ __device__ __forceinline__ NodeStateT<V> node_state_t(const V d[9], V eps, V inv
       solid_state(s, c);
     }
   } else {
-    if (DYN) {  // a solid lane's value is computed and not used
-      inv_k.x = dynamic_inv_k(inv_k.x, s.drho_s.x, kn0.x, a);
-      inv_k.y = dynamic_inv_k(inv_k.y, s.drho_s.y, kn0.y, a);
-    }
+    if (DYN) inv_k = dynamic_inv_k(inv_k, s.drho_s, kn0, a);  // a solid lane's value is unused
     const bool px = eps.x > 0.0f, py = eps.y > 0.0f;
     if (px && py) {  // the common case: two permeable nodes
       porous_state(s, eps, inv_k, c, a);
