@@ -143,10 +143,14 @@ constexpr int kHeadBytes = 128;
 static_assert(sizeof(TileHead) <= kHeadBytes && sizeof(TileHead) % 16 == 0, "tile header");
 // Stage configuration of the batched kernel.  Its consumers hold more per
 // tile (the instance's buffers, geometry and scale) than the single-lattice
-// ones; 12 consumer warps (13 with the producer: 128 registers a thread)
-// keep them in registers, where 16 would spill, and each thread takes two
-// or three node pairs per tile (on 512 instances: FP16 124 GLUPS against
-// 117, FP32 82 against 73).
+// ones: ~108 registers a thread.  Registers are split between the SM's four
+// schedulers (16 K each) and a block's warps spread over them, so a block of
+// 17 warps (16 consumers and the producer) leaves 96 registers a thread and
+// spills, while 16 warps leave 128.  FP16: 15 consumer warps, tiles of 2880
+// nodes (three pairs a thread), 3 stages (256 instances: 131.7 -> 142.9
+// GLUPS against 12 warps x 2304 x 3; the larger tiles also spread the
+// per-tile header and column-edge work over more nodes).  FP32: 12 consumer
+// warps, 1536-node tiles, two pairs a thread (at the copy roofline).
 template <class S>
 struct BatchCfg;
 template <>
@@ -157,8 +161,8 @@ struct BatchCfg<StoreF32> {
 };
 template <>
 struct BatchCfg<StoreF16> {
-  static constexpr int W = 2304, H = 1, A = 8, STAGES = 3;
-  static constexpr int WARPS = 12;
+  static constexpr int W = 2880, H = 1, A = 8, STAGES = 3;
+  static constexpr int WARPS = 15;
   static constexpr bool KN0 = false;
 };
 template <class S>
