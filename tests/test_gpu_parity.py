@@ -297,13 +297,15 @@ def test_checkpoint_restart_bitwise(storage):
 
 @pytest.mark.parametrize("storage", [FP32, FP16])
 @pytest.mark.parametrize("walls,pressure", [(True, True), (False, False), (True, False)])
-def test_staged_matches_direct(storage, walls, pressure):
+@pytest.mark.parametrize("nx", [300, 301])
+def test_staged_matches_direct(storage, walls, pressure, nx):
     """Same arithmetic in both kernels, every rounding written out: the
     staged kernel's packed node pairs give the direct kernel's one-node
     results bit for bit.  FP16 is compared with round-to-nearest (the
-    stochastic streams of the two kernels differ)."""
-    med = media.random_medium(300, 41, seed=12, p_open=0.1, p_solid=0.1, log10_k_range=(-3, 0))
-    case = Case(300, 41, tau=0.7, G=(1e-5, 0.0), walls=walls, pressure=pressure,
+    stochastic streams of the two kernels differ).  An odd width leaves a
+    lone last node in every row (stored as a pair with the row padding)."""
+    med = media.random_medium(nx, 41, seed=12, p_open=0.1, p_solid=0.1, log10_k_range=(-3, 0))
+    case = Case(nx, 41, tau=0.7, G=(1e-5, 0.0), walls=walls, pressure=pressure,
                 rho_in=1.001, rho_out=0.999, forchheimer=1, medium=med)
     a = gpu_sim(case, storage, kernel=STAGED, fp16_rounding=RN)
     b = gpu_sim(case, storage, kernel=DIRECT, fp16_rounding=RN)
@@ -317,14 +319,15 @@ def test_staged_matches_direct(storage, walls, pressure):
 
 
 @pytest.mark.parametrize("walls,pressure", [(True, True), (False, False)])
-def test_staged_matches_direct_dynamic_kn(walls, pressure):
+@pytest.mark.parametrize("nx", [300, 301])
+def test_staged_matches_direct_dynamic_kn(walls, pressure, nx):
     """FP16 with a dynamic Kn: the staged kernel (which stages the Kn plane
     beside the medium) and the direct kernel form f_c(Kn0 p0 / p) node by
     node with the same operations, so the populations agree bit for bit
     (round-to-nearest)."""
-    med = media.random_medium(300, 41, seed=14, p_open=0.1, p_solid=0.1, log10_k_range=(-3, 0),
+    med = media.random_medium(nx, 41, seed=14, p_open=0.1, p_solid=0.1, log10_k_range=(-3, 0),
                               kn_range=(0.0, 5.0))
-    case = Case(300, 41, tau=0.7, G=(1e-5, 0.0), walls=walls, pressure=pressure,
+    case = Case(nx, 41, tau=0.7, G=(1e-5, 0.0), walls=walls, pressure=pressure,
                 rho_in=1.001, rho_out=0.999, forchheimer=1, medium=med, kn_beta=100.0)
     a = gpu_sim(case, FP16, kernel=STAGED, fp16_rounding=RN)
     b = gpu_sim(case, FP16, kernel=DIRECT, fp16_rounding=RN)
