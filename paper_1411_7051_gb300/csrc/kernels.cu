@@ -234,18 +234,72 @@ __device__ __forceinline__ void block_reduce_store(double v[kNQ], double *partia
   }
 }
 
+// ------------------------------------------------ FP32-pair arithmetic
+// Pairs of FP32 numbers (value = hi + lo) carrying ~44 significant bits:
+// exact sums (Knuth's two-sum) and exact products (fma of the product and
+// its negation), the standard error-free transformations.  FP64 arithmetic
+// runs at ~1/64 of the FP32 rate on this GPU; the precompute and the
+// per-thread parts of the reductions use these pairs instead.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+  F2 s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ F2 f2_mul(F2 x, F2 y) {
+  F2 p = two_prod(x.hi, y.hi);
+  const float c = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+  return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
+}
+// n / d from an approximate reciprocal r of d.hi (relative error e ~ 2^-23):
+// q1 = n.hi r is off by ~e, the remainder n - q1 d is formed exactly enough
+// (~2^-48 of n), and its quotient by the same r corrects q1 to a relative
+// error of order e^2 -- one Newton step on the quotient.
+__device__ __forceinline__ F2 f2_div(F2 n, F2 d) {
+  const float r = rcp_approx(d.hi);
+  const float q1 = __fmul_rn(n.hi, r);
+  const F2 qd = f2_mul({q1, 0.0f}, d);           // q1 d
+  const F2 rem = f2_add(n, {-qd.hi, -qd.lo});     // n - q1 d
+  return fast_two_sum(q1, __fmul_rn(rem.hi, r));
+}
+// acc += x (x an FP32 value)
+__device__ __forceinline__ void f2_acc(F2 &acc, float x) {
+  const F2 s = two_sum(acc.hi, x);
+  acc = fast_two_sum(s.hi, __fadd_rn(s.lo, acc.lo));
+}
+
 // ------------------------------------------- macroscopic / reduction kernel
-// Rows blockIdx.y, blockIdx.y + gridDim.y, ...: each thread adds the FP64
-// terms of its nodes one by one and takes part in one block reduction at
-// the end (FP64 arithmetic is slow on this GPU; a reduction tree per node
-// cost six times the per-node work).
+// Rows blockIdx.y, blockIdx.y + gridDim.y, ...: each thread adds the terms
+// of its nodes (some 27 at 4096^2) one by one in FP32 pairs and takes part
+// in one FP64 block reduction at the end (FP64 arithmetic is slow on this
+// GPU: a reduction tree per node cost six times the per-node work, and FP64
+// per-node sums 0.48 ms at 4096^2).  The squares are exact products, the
+// velocity differences of the residual exact sums; a thread's pair sums
+// are good to ~2^-44 relative.
 template <class S>
 __global__ void __launch_bounds__(kMacroBX)
     macro_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
                  const float2 *__restrict__ med, const MacroOut o) {
   const int x = blockIdx.x * kMacroBX + threadIdx.x;
   const long long n = (long long)a.nx * a.ny;
-  double v[kNQ] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  F2 sux = {0.0f, 0.0f}, suy = {0.0f, 0.0f}, sdr = {0.0f, 0.0f}, su2 = {0.0f, 0.0f},
+     sdu = {0.0f, 0.0f};
+  unsigned nonfinite = 0;
   for (int y = blockIdx.y; y < a.ny && x < a.nx; y += gridDim.y) {
     const bool wall = a.walls && (y == 0 || y == a.ny - 1);
     const long long j = (long long)y * a.nx + x;
@@ -282,25 +336,31 @@ __global__ void __launch_bounds__(kMacroBX)
       for (int i = 0; i < 9; ++i) o.pops[i * n + j] = w[i] * r0 + (double)d[i] * is;
     }
     if (o.partials) {
-      const double ux = s.ux, uy = s.uy;
       const bool finite = isfinite(s.ux) && isfinite(s.uy) && isfinite(s.rho);
       if (finite) {
-        v[0] += ux;
-        v[1] += uy;
-        v[2] += (double)drho;
-        v[3] += ux * ux + uy * uy;
+        f2_acc(sux, s.ux);
+        f2_acc(suy, s.uy);
+        f2_acc(sdr, drho);
+        su2 = f2_add(su2, f2_add(two_prod(s.ux, s.ux), two_prod(s.uy, s.uy)));
       } else {
-        v[5] += 1.0;
+        ++nonfinite;
       }
       if (o.uprev) {
         const float2 up = o.uprev[jp];
-        const double dx = ux - (double)up.x, dy = uy - (double)up.y;
-        if (finite) v[4] += dx * dx + dy * dy;
+        if (finite) {
+          const F2 dx = two_sum(s.ux, -up.x), dy = two_sum(s.uy, -up.y);
+          sdu = f2_add(sdu, f2_add(f2_mul(dx, dx), f2_mul(dy, dy)));
+        }
         if (o.update_prev) o.uprev[jp] = make_float2(s.ux, s.uy);
       }
     }
   }
-  if (o.partials) block_reduce_store<kMacroBX>(v, o.partials);
+  if (o.partials) {
+    double v[kNQ] = {(double)sux.hi + (double)sux.lo, (double)suy.hi + (double)suy.lo,
+                     (double)sdr.hi + (double)sdr.lo, (double)su2.hi + (double)su2.lo,
+                     (double)sdu.hi + (double)sdu.lo, (double)nonfinite};
+    block_reduce_store<kMacroBX>(v, o.partials);
+  }
 }
 
 // Up to 16 blocks of 256 threads on each of 152 SMs.
@@ -485,51 +545,11 @@ __device__ __forceinline__ double inv_ka(double k, double K, int model) {
   return (a * (1.0 + K)) / (k * fma(1.358, K, a) * fma(5.0, K, 1.0));
 }
 
-// ---- the same fraction in FP32-pair arithmetic (value = hi + lo) ----------
+// ---- the same fraction in FP32-pair arithmetic (the F2 helpers above) ----
 // FP64 instructions are the bottleneck of the precompute on this GPU, so
-// for the usual ranges of k_i and Kn the fraction is evaluated with pairs
-// of FP32 numbers carrying ~44 significant bits: exact sums (Knuth's
-// two-sum) and exact products (fma of the product and its negation), the
-// standard error-free transformations.  Beside the FP32 power of Kn (as in
-// inv_ka) the result differs from the FP64 one by ~2^-40 before its final
-// rounding to FP32.
-struct F2 {
-  float hi, lo;
-};
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ F2 two_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
-}
-__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
-  F2 s = two_sum(x.hi, y.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
-}
-__device__ __forceinline__ F2 f2_mul(F2 x, F2 y) {
-  F2 p = two_prod(x.hi, y.hi);
-  const float c = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
-  return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
-}
-// n / d from an approximate reciprocal r of d.hi (relative error e ~ 2^-23):
-// q1 = n.hi r is off by ~e, the remainder n - q1 d is formed exactly enough
-// (~2^-48 of n), and its quotient by the same r corrects q1 to a relative
-// error of order e^2 -- one Newton step on the quotient.
-__device__ __forceinline__ F2 f2_div(F2 n, F2 d) {
-  const float r = rcp_approx(d.hi);
-  const float q1 = __fmul_rn(n.hi, r);
-  const F2 qd = f2_mul({q1, 0.0f}, d);           // q1 d
-  const F2 rem = f2_add(n, {-qd.hi, -qd.lo});     // n - q1 d
-  return fast_two_sum(q1, __fmul_rn(rem.hi, r));
-}
+// for the usual ranges of k_i and Kn the fraction is evaluated with FP32
+// pairs.  Beside the FP32 power of Kn (as in inv_ka) the result differs from
+// the FP64 one by ~2^-40 before its final rounding to FP32.
 // A double in [2^-60, 2^60] (not 0) as hi + lo with integer operations only: hi
 // keeps the leading 24 bits, lo the next 29 (rounded to 24; the pair then
 // carries d to a relative 2^-48).
