@@ -291,8 +291,10 @@ __device__ __forceinline__ void f2_acc(F2 &acc, float x) {
 // per-node sums 0.48 ms at 4096^2).  The squares are exact products, the
 // velocity differences of the residual exact sums; a thread's pair sums
 // are good to ~2^-44 relative.
+// Four resident blocks a SM (64 registers a thread; 2 at the compiler's own
+// 116): 0.37 -> 0.28 ms a lbmp_permeability call at 4096^2.
 template <class S>
-__global__ void __launch_bounds__(kMacroBX)
+__global__ void __launch_bounds__(kMacroBX, 4)
     macro_kernel(const StepArgs a, const typename S::T *__restrict__ fin,
                  const float2 *__restrict__ med, const MacroOut o) {
   const int x = blockIdx.x * kMacroBX + threadIdx.x;
