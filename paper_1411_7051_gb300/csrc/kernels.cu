@@ -394,44 +394,27 @@ cudaError_t launch_macro(int storage, const StepArgs &a, const void *fin,
 // ------------------------------------------------------------- finalize
 constexpr int kFinBX = 256;
 
-// Sums (or maxima) of nq <= 8 quantities over nblocks partials, in a fixed
-// order: the block's warps are shared out among the quantities (one each
-// for the six reductions, all eight for one), a lane combines every 32 wpq-th
-// partial in four interleaved accumulators, then the lanes by shuffles and
-// the warps of a quantity in order.
 __global__ void __launch_bounds__(kFinBX)
     finalize_kernel(const double *__restrict__ partials, int nblocks, int nq,
                     double *__restrict__ out, unsigned max_mask) {
-  constexpr int kWarps = kFinBX / 32;
-  __shared__ double sh[kWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wpq = nq < kWarps ? kWarps / nq : 1;  // warps per quantity
-  const int q = warp / wpq, sub = warp - q * wpq;
-  if (q < nq) {
+  __shared__ double sh[kFinBX];
+  for (int q = 0; q < nq; ++q) {
     const bool mx = (max_mask >> q) & 1u;
-    auto op = [mx](double u, double v) { return mx ? fmax(u, v) : u + v; };
-    const int stride = 32 * wpq;
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-    int b = sub * 32 + lane;
-    for (; b + 3 * stride < nblocks; b += 4 * stride) {
-      t0 = op(t0, partials[(long long)b * nq + q]);
-      t1 = op(t1, partials[(long long)(b + stride) * nq + q]);
-      t2 = op(t2, partials[(long long)(b + 2 * stride) * nq + q]);
-      t3 = op(t3, partials[(long long)(b + 3 * stride) * nq + q]);
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kFinBX) {
+      const double v = partials[(long long)b * nq + q];
+      t = mx ? fmax(t, v) : t + v;
     }
-    for (; b < nblocks; b += stride) t0 = op(t0, partials[(long long)b * nq + q]);
-    double t = op(op(t0, t1), op(t2, t3));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t = op(t, __shfl_down_sync(0xffffffffu, t, off));
-    if (lane == 0) sh[warp] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < nq) {
-    const int qq = threadIdx.x;
-    const bool mx = (max_mask >> qq) & 1u;
-    double t = sh[qq * wpq];
-    for (int w = 1; w < wpq; ++w) t = mx ? fmax(t, sh[qq * wpq + w]) : t + sh[qq * wpq + w];
-    out[qq] = t;
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = kFinBX / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w)
+        sh[threadIdx.x] = mx ? fmax(sh[threadIdx.x], sh[threadIdx.x + w])
+                             : sh[threadIdx.x] + sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sh[0];
+    __syncthreads();
   }
 }
 
