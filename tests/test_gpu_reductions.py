@@ -124,3 +124,21 @@ def test_steady_channel_residual_tracks_the_oracle(orc):
             assert abs(r_gpu / r_orc - 1) <= 1e-3, (k, r_gpu, r_orc)
             checked += 1
     assert checked >= 5
+
+
+def test_run_to_steady_on_the_gpu():
+    """Sim.run_to_steady: the validation channel reaches a residual of 1e-6
+    over 100-step windows (FP32 velocities floor near 1e-7), the last window
+    is below the bound, and an unreachable bound raises after its step limit
+    instead of looping."""
+    med = media.channel(64, 33, 0.7, 1e-3, 0.1)
+    case = Case(64, 33, tau=0.8, G=(1e-6, 0.0), walls=True, medium=med)
+    gs = gpu_sim(case, FP32)
+    r = gs.run_to_steady(tol=1e-6, check_every=100, max_steps=50_000)
+    assert 0.0 <= r < 1e-6
+    steps = gs.info().steps
+    assert 0 < steps < 50_000 and steps % 100 == 0
+    gs.step(100)
+    assert gs.residual() < 1e-6
+    with pytest.raises(RuntimeError):
+        gpu_sim(case, FP32).run_to_steady(tol=1e-30, check_every=100, max_steps=1000)
