@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "nvtx_range.h"
 #include "lattice.cuh"
 #include "lbmp.h"
 #include "staged.cuh"
@@ -772,6 +773,7 @@ lbmp_status lbmp_batch_class(const lbmp_params *p, int32_t count, const int32_t 
 
 lbmp_status lbmp_batch_create(const lbmp_params *pin, int32_t count, const int32_t *nx,
                               const int32_t *ny, lbmp_batch **out) {
+  const lbmp::NvtxRange nvtx_range("lbmp_batch_create");
   try {
     if (!pin || !nx || !ny || !out) return bfail(LBMP_EINVAL, "lbmp_batch_create: NULL argument");
     *out = nullptr;
@@ -937,6 +939,7 @@ lbmp_status lbmp_batch_destroy(lbmp_batch *b) {
 
 lbmp_status lbmp_batch_set_fields(lbmp_batch *b, int32_t i, const double *eps, const double *k_i,
                                   const double *kn, int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_batch_set_fields");
   try {
     if (!b || !eps || !k_i || !kn) return bfail(LBMP_EINVAL, "lbmp_batch_set_fields: NULL argument");
     if (i < 0 || i >= b->count) return bfail(LBMP_EINVAL, "instance %d out of range", i);
@@ -1017,6 +1020,7 @@ lbmp_status lbmp_batch_set_fields(lbmp_batch *b, int32_t i, const double *eps, c
 }
 
 lbmp_status lbmp_batch_step(lbmp_batch *b, int64_t n) {
+  const lbmp::NvtxRange nvtx_range("lbmp_batch_step");
   try {
     if (!b) return bfail(LBMP_EINVAL, "lbmp_batch_step: NULL batch");
     if (n < 0) return bfail(LBMP_EINVAL, "n must be >= 0");
@@ -1030,6 +1034,7 @@ lbmp_status lbmp_batch_step(lbmp_batch *b, int64_t n) {
 }
 
 lbmp_status lbmp_batch_synchronize(lbmp_batch *b) {
+  const lbmp::NvtxRange nvtx_range("lbmp_batch_synchronize");
   if (!b) return bfail(LBMP_EINVAL, "NULL batch");
   BCK(cudaSetDevice(b->device));
   BCK(cudaStreamSynchronize(b->stream));
@@ -1041,6 +1046,7 @@ lbmp_status lbmp_batch_synchronize(lbmp_batch *b) {
 
 lbmp_status lbmp_batch_tune_cached(lbmp_batch *b, int32_t steps, int32_t *chosen,
                                    double *ms_per_step, int32_t *from_cache) {
+  const lbmp::NvtxRange nvtx_range("lbmp_batch_tune_cached");
   try {
     if (!b) return bfail(LBMP_EINVAL, "NULL batch");
     if (steps < 1) return bfail(LBMP_EINVAL, "steps must be >= 1");
@@ -1103,6 +1109,7 @@ lbmp_status lbmp_batch_set_shape(lbmp_batch *b, int32_t shape) {
 }
 
 lbmp_status lbmp_batch_permeability(lbmp_batch *b, double *k_g, double *u_mean) {
+  const lbmp::NvtxRange nvtx_range("lbmp_batch_permeability");
   try {
     if (!b) return bfail(LBMP_EINVAL, "NULL batch");
     if (!all_fields(b)) return bfail(LBMP_ESTATE, "every instance needs its fields");
@@ -1149,6 +1156,7 @@ lbmp_status lbmp_batch_permeability(lbmp_batch *b, double *k_g, double *u_mean) 
 }
 
 lbmp_status lbmp_batch_populations(lbmp_batch *b, int32_t i, double *f, int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_batch_populations");
   try {
     if (!b || !f) return bfail(LBMP_EINVAL, "NULL argument");
     if (i < 0 || i >= b->count) return bfail(LBMP_EINVAL, "instance %d out of range", i);
@@ -1178,6 +1186,7 @@ lbmp_status lbmp_batch_populations(lbmp_batch *b, int32_t i, double *f, int32_t 
 }
 
 lbmp_status lbmp_batch_tune(lbmp_batch *b, int32_t steps, int32_t *chosen, double *ms_per_step) {
+  const lbmp::NvtxRange nvtx_range("lbmp_batch_tune");
   try {
     if (!b) return bfail(LBMP_EINVAL, "NULL batch");
     if (steps < 1) return bfail(LBMP_EINVAL, "steps must be >= 1");

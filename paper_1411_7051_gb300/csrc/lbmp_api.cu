@@ -17,6 +17,7 @@
 #include "lbmp.h"
 #include "kernels.h"
 #include "context.h"
+#include "nvtx_range.h"
 
 using lbmp::StepArgs;
 
@@ -338,6 +339,7 @@ lbmp_status lbmp_physical_medium(int64_t n, const double *eps, const double *d, 
 }
 
 lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
+  const lbmp::NvtxRange nvtx_range("lbmp_create");
   try {
     if (!pin || !out) return fail(LBMP_EINVAL, "lbmp_create: NULL argument");
     *out = nullptr;
@@ -425,6 +427,7 @@ lbmp_status lbmp_create(const lbmp_params *pin, lbmp_ctx **out) {
 }
 
 lbmp_status lbmp_destroy(lbmp_ctx *c) {
+  const lbmp::NvtxRange nvtx_range("lbmp_destroy");
   try {
     release(c);
     return LBMP_OK;
@@ -435,6 +438,7 @@ lbmp_status lbmp_destroy(lbmp_ctx *c) {
 
 lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
                             const double *kn, int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_set_fields");
   try {
     if (!c || !eps || !k_i || !kn) return fail(LBMP_EINVAL, "lbmp_set_fields: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
@@ -545,6 +549,7 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
 }
 
 lbmp_status lbmp_step(lbmp_ctx *c, int64_t n) {
+  const lbmp::NvtxRange nvtx_range("lbmp_step");
   try {
     if (!c) return fail(LBMP_EINVAL, "lbmp_step: NULL context");
     if (n < 0) return fail(LBMP_EINVAL, "lbmp_step: n must be >= 0");
@@ -576,6 +581,7 @@ lbmp_status lbmp_step(lbmp_ctx *c, int64_t n) {
 }
 
 lbmp_status lbmp_synchronize(lbmp_ctx *c) {
+  const lbmp::NvtxRange nvtx_range("lbmp_synchronize");
   if (!c) return fail(LBMP_EINVAL, "lbmp_synchronize: NULL context");
   lbmp_status st = set_device(c);
   if (st) return st;
@@ -585,6 +591,7 @@ lbmp_status lbmp_synchronize(lbmp_ctx *c) {
 
 lbmp_status lbmp_macroscopic(lbmp_ctx *c, double *rho, double *ux, double *uy,
                              int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_macroscopic");
   try {
     if (!c) return fail(LBMP_EINVAL, "lbmp_macroscopic: NULL context");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
@@ -621,6 +628,7 @@ lbmp_status lbmp_macroscopic(lbmp_ctx *c, double *rho, double *ux, double *uy,
 }
 
 lbmp_status lbmp_apparent_permeability(lbmp_ctx *c, double *ka, int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_apparent_permeability");
   try {
     if (!c || !ka) return fail(LBMP_EINVAL, "lbmp_apparent_permeability: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
@@ -648,6 +656,7 @@ lbmp_status lbmp_apparent_permeability(lbmp_ctx *c, double *ka, int32_t where) {
 }
 
 lbmp_status lbmp_populations(lbmp_ctx *c, double *f, int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_populations");
   try {
     if (!c || !f) return fail(LBMP_EINVAL, "lbmp_populations: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
@@ -675,6 +684,7 @@ lbmp_status lbmp_populations(lbmp_ctx *c, double *f, int32_t where) {
 }
 
 lbmp_status lbmp_set_populations(lbmp_ctx *c, const double *f, int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_set_populations");
   try {
     if (!c || !f) return fail(LBMP_EINVAL, "lbmp_set_populations: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
@@ -701,6 +711,7 @@ lbmp_status lbmp_set_populations(lbmp_ctx *c, const double *f, int32_t where) {
 }
 
 lbmp_status lbmp_permeability(lbmp_ctx *c, double *k_g, double *u_mean) {
+  const lbmp::NvtxRange nvtx_range("lbmp_permeability");
   try {
     if (!c) return fail(LBMP_EINVAL, "lbmp_permeability: NULL context");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_permeability: no fields set");
@@ -725,6 +736,7 @@ lbmp_status lbmp_permeability(lbmp_ctx *c, double *k_g, double *u_mean) {
 
 lbmp_status lbmp_velocity_histogram(lbmp_ctx *c, int32_t nbins, double *umax,
                                     int64_t *counts) {
+  const lbmp::NvtxRange nvtx_range("lbmp_velocity_histogram");
   try {
     if (!c || !counts) return fail(LBMP_EINVAL, "lbmp_velocity_histogram: NULL argument");
     if (nbins < 1 || nbins > lbmp::kMaxHistBins)
@@ -768,6 +780,7 @@ lbmp_status lbmp_velocity_histogram(lbmp_ctx *c, int32_t nbins, double *umax,
 }
 
 lbmp_status lbmp_residual(lbmp_ctx *c, double *r) {
+  const lbmp::NvtxRange nvtx_range("lbmp_residual");
   try {
     if (!c || !r) return fail(LBMP_EINVAL, "lbmp_residual: NULL argument");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_residual: no fields set");
@@ -786,6 +799,7 @@ lbmp_status lbmp_residual(lbmp_ctx *c, double *r) {
 }
 
 lbmp_status lbmp_mass(lbmp_ctx *c, double *m) {
+  const lbmp::NvtxRange nvtx_range("lbmp_mass");
   try {
     if (!c || !m) return fail(LBMP_EINVAL, "lbmp_mass: NULL argument");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_mass: no fields set");
@@ -808,6 +822,7 @@ lbmp_status lbmp_state_size(lbmp_ctx *c, size_t *bytes) {
 }
 
 lbmp_status lbmp_get_state(lbmp_ctx *c, void *buf, size_t bytes, int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_get_state");
   try {
     if (!c || !buf) return fail(LBMP_EINVAL, "lbmp_get_state: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
@@ -838,6 +853,7 @@ lbmp_status lbmp_get_state(lbmp_ctx *c, void *buf, size_t bytes, int32_t where) 
 }
 
 lbmp_status lbmp_set_state(lbmp_ctx *c, const void *buf, size_t bytes, int32_t where) {
+  const lbmp::NvtxRange nvtx_range("lbmp_set_state");
   try {
     if (!c || !buf) return fail(LBMP_EINVAL, "lbmp_set_state: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
