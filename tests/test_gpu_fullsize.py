@@ -5,7 +5,8 @@ on sampled nodes: from the GPU's own state at level K (downloaded exactly,
 FP64), the oracle's single-node collision of the nine upstream neighbours
 gives the populations of level K + 1 at each sampled node, which must match
 the GPU's.  Interior columns only (the pressure columns are covered by the
-small-lattice tests).  Also checked: the largest row count the API accepts.
+small-lattice tests).  Also checked: the largest row count the API accepts,
+and a lattice whose population planes lie beyond 2^31 elements.
 """
 import numpy as np
 import pytest
@@ -37,7 +38,6 @@ def _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=0, kn_beta=0
     f1 = sim.populations(device=True)
     got = f1[:, torch.as_tensor(ys, device="cuda"), torch.as_tensor(xs, device="cuda")].cpu().numpy().T
     del f1
-    ka = med.k_i * np.vectorize(orc.fc)(med.kn)
     params = orc.make_params(nx, ny, tau=cfg.tau, G=cfg.G,
                              bc_x=orc.BC_PRESSURE if cfg.bc_x else orc.BC_PERIODIC,
                              bc_y=orc.BC_WALLS if cfg.bc_y else orc.BC_PERIODIC,
@@ -48,7 +48,7 @@ def _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=0, kn_beta=0
         """k_a of a source node: static, or with a dynamic Kn at the pressure
         of its own post-stream state f (p / p0 = 1 + beta (rho - rho0))."""
         if kn_beta == 0.0:
-            return ka[sy, sx]
+            return med.k_i[sy, sx] * orc.fc(med.kn[sy, sx])
         q = 1.0 + kn_beta * (float(np.sum(f)) - 1.0)
         return med.k_i[sy, sx] * orc.fc(med.kn[sy, sx] / q)
     exp = np.zeros_like(got)
@@ -106,3 +106,35 @@ def test_largest_row_count(orc, storage):
         sim.set_fields(med.eps, med.k_i, med.kn)
         sim.step(40)
         _sampled_one_step(orc, sim, cfg, med, storage, nsamp=800, seed=3)
+
+
+@pytest.fixture(scope="module")
+def medium_16k():
+    n = 16384
+    return media.random_medium(n, n, seed=93, log10_k_range=(-3, 0), p_open=0.02, p_solid=0.02)
+
+
+@pytest.mark.parametrize("storage", [lbmp.STORE_FP32, lbmp.STORE_FP16])
+def test_offsets_beyond_int32(orc, medium_16k, storage):
+    """16384 x 16384 (row pitch 16448): a population buffer's nine planes span
+    2.4e9 elements, so every update reads and writes plane offsets above 2^31
+    elements (above 2^32 bytes), and a staged launch walks 131 000 tiles.
+    Pressure x, plates y, Forchheimer, AUTO kernel: one step on sampled nodes
+    against the oracle after 8 steps, and the mean velocity of
+    lbmp_permeability against the FP64 sum of the velocity field that
+    lbmp_macroscopic (another kernel) reports over the fluid rows."""
+    import torch
+    med = medium_16k
+    ny, nx = med.eps.shape
+    cfg = lbmp.SimConfig(nx, ny, tau=0.8, bc_x=lbmp.BCX_PRESSURE, bc_y=lbmp.BCY_WALLS,
+                         rho_in=1.002, rho_out=0.998, forchheimer=1, storage=storage)
+    with lbmp.Sim(cfg) as sim:
+        sim.set_fields(med.eps, med.k_i, med.kn)
+        sim.step(8)
+        _sampled_one_step(orc, sim, cfg, med, storage, nsamp=1500, seed=5)
+        kg, um = sim.permeability()
+        _, ux, _ = sim.macroscopic(device=True)
+        ref = float(ux[1:ny - 1].sum(dtype=torch.float64)) / (nx * (ny - 2))
+        del ux
+    assert np.isfinite(kg) and kg > 0.0
+    assert um == pytest.approx(ref, rel=1e-9, abs=0), (um, ref)
