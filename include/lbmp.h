@@ -392,7 +392,7 @@ lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out);
  * (e.g. 4096 x 4096); larger lattices get LBMP_EINVAL.  Every call uses the
  * same array: calls that overlap on the GPU (other streams, other threads)
  * race.  The first call on each device looks up the array's device address
- * (once, under a lock); make that first call before any stream capture.
+ * (once, under a lock).
  * The sizes of the caller's arrays cannot be checked here: they must hold
  * what nx and ny imply.
  * Errors: EINVAL (NULL pointer, a parameter lbmp_create would reject among
