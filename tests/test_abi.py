@@ -75,6 +75,29 @@ def test_null_arguments(L):
     assert L.lbmp_get_info(None, None) == lbmp.EINVAL
 
 
+@pytest.mark.parametrize("sizes,kw,needle", [
+    ([], {}, "count must be"),
+    ([(64, 32), (0, 16)], {}, "nx, ny"),
+    ([(64, 32), (40, 70000)], {}, "ny must be"),
+    ([(64, 32)], {"kn_beta": 5.0}, "dynamic Kn"),
+    ([(64, 32)], {"tau": 0.4}, "tau"),
+    ([(64, 32), (2, 16)], {"bc_x": lbmp.BCX_PRESSURE}, "nx >= 3"),
+    ([(64, 32), (16, 2)], {"bc_y": lbmp.BCY_WALLS}, "ny >= 3"),
+])
+def test_batch_create_rejects_bad_parameters(L, sizes, kw, needle):
+    """lbmp_batch_create checks the count and every instance under the rules
+    of lbmp_create before anything is allocated (no GPU needed)."""
+    p = lbmp.SimConfig(**{"nx": 1, "ny": 1, **kw}).to_params(None)
+    n = len(sizes)
+    nx = (ctypes.c_int32 * max(n, 1))(*[s[0] for s in sizes])
+    ny = (ctypes.c_int32 * max(n, 1))(*[s[1] for s in sizes])
+    h = ctypes.c_void_p()
+    st = L.lbmp_batch_create(ctypes.byref(p), n, nx, ny, ctypes.byref(h))
+    assert st == lbmp.EINVAL, (st, lbmp.last_error())
+    assert needle in lbmp.last_error()
+    assert not h.value
+
+
 @pytest.mark.parametrize("kw,needle", [
     ({"kn_model": 7}, "kn_model"),
     ({"bc_x": 5}, "bc_x"),
