@@ -130,6 +130,9 @@ const char *lbmp_last_error(void);
 
 /* Create a context on the current CUDA device: validates p, allocates the
  * two population buffers, the per-node medium and the reduction scratch.
+ * Every later call on the context (and on a batch, created the same way)
+ * runs on that device and gives the caller's current device back before it
+ * returns; device pointers passed to it must be memory of that device.
  * Errors: EINVAL (bad parameters; nothing allocated), ENOMEM, ECUDA.
  * Section III (Eq. 12-17) defines the state the context holds. */
 lbmp_status lbmp_create(const lbmp_params *p, lbmp_ctx **out);

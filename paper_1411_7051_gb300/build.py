@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbmp.so")
 SOURCES = ["kernels.cu", "lbmp_api.cu", "noalloc.cu", "batch.cu", "adjoint.cu"]
-HEADERS = ["lattice.cuh", "kernels.h", "staged.cuh", "wide.cuh", "context.h", "nvtx_range.h"]
+HEADERS = ["lattice.cuh", "kernels.h", "staged.cuh", "wide.cuh", "context.h", "nvtx_range.h", "device_scope.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "-Xptxas", "-O3", "--expt-relaxed-constexpr"]

@@ -34,6 +34,7 @@
 #include <tuple>
 
 #include "context.h"
+#include "device_scope.h"
 #include "kernels.h"
 #include "lattice.cuh"
 #include "lbmp.h"
@@ -528,7 +529,8 @@ extern "C" lbmp_status lbmp_permeability_gradient(lbmp_ctx *c, int64_t nsteps, i
       return afail(LBMP_EINVAL, "lbmp_permeability_gradient needs FP32 storage");
     if (c->p.kn_beta != 0.0)
       return afail(LBMP_EINVAL, "lbmp_permeability_gradient: a dynamic Kn is not available");
-    ACK(cudaSetDevice(c->device));
+    const DeviceScope device_scope(c->device);
+    ACK(device_scope.err);
     if (every == 0) every = (int64_t)std::ceil(std::sqrt((double)nsteps));
     every = std::min(every, nsteps);
     const int64_t nseg = (nsteps + every - 1) / every;

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "device_scope.h"
 #include "nvtx_range.h"
 #include "lattice.cuh"
 #include "lbmp.h"
@@ -566,7 +567,7 @@ void bfree_graphs(lbmp_batch *b) {
 
 void brelease(lbmp_batch *b) {
   if (!b) return;
-  cudaSetDevice(b->device);
+  const DeviceScope device_scope(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   bfree_graphs(b);
   for (void *p : b->allocs) cudaFree(p);
@@ -944,7 +945,8 @@ lbmp_status lbmp_batch_set_fields(lbmp_batch *b, int32_t i, const double *eps, c
     if (!b || !eps || !k_i || !kn) return bfail(LBMP_EINVAL, "lbmp_batch_set_fields: NULL argument");
     if (i < 0 || i >= b->count) return bfail(LBMP_EINVAL, "instance %d out of range", i);
     if (where != LBMP_HOST && where != LBMP_DEVICE) return bfail(LBMP_EINVAL, "bad where");
-    BCK(cudaSetDevice(b->device));
+    const DeviceScope device_scope(b->device);
+    BCK(device_scope.err);
     BatchInst &I = b->h_inst[i];
     lbmp::StepArgs &a = I.a;
     const size_t n = (size_t)a.nx * a.ny;
@@ -1026,7 +1028,8 @@ lbmp_status lbmp_batch_step(lbmp_batch *b, int64_t n) {
     if (n < 0) return bfail(LBMP_EINVAL, "n must be >= 0");
     if (!all_fields(b)) return bfail(LBMP_ESTATE, "lbmp_batch_step: every instance needs its fields");
     if (n == 0) return LBMP_OK;
-    BCK(cudaSetDevice(b->device));
+    const DeviceScope device_scope(b->device);
+    BCK(device_scope.err);
     return do_step(b, n);
   } catch (...) {
     return bfail(LBMP_ECUDA, "lbmp_batch_step: unexpected exception");
@@ -1036,7 +1039,8 @@ lbmp_status lbmp_batch_step(lbmp_batch *b, int64_t n) {
 lbmp_status lbmp_batch_synchronize(lbmp_batch *b) {
   const lbmp::NvtxRange nvtx_range("lbmp_batch_synchronize");
   if (!b) return bfail(LBMP_EINVAL, "NULL batch");
-  BCK(cudaSetDevice(b->device));
+  const DeviceScope device_scope(b->device);
+  BCK(device_scope.err);
   BCK(cudaStreamSynchronize(b->stream));
   unsigned err = 0;
   BCK(cudaMemcpy(&err, b->d_err, sizeof(err), cudaMemcpyDeviceToHost));
@@ -1101,7 +1105,8 @@ lbmp_status lbmp_batch_set_shape(lbmp_batch *b, int32_t shape) {
     if (!b) return bfail(LBMP_EINVAL, "NULL batch");
     if (shape < 0 || shape >= lbmp::kNumShapes)
       return bfail(LBMP_EINVAL, "shape must be in [0, %d)", lbmp::kNumShapes);
-    BCK(cudaSetDevice(b->device));
+    const DeviceScope device_scope(b->device);
+    BCK(device_scope.err);
     return set_shape(b, shape);
   } catch (...) {
     return bfail(LBMP_ECUDA, "lbmp_batch_set_shape: unexpected exception");
@@ -1113,7 +1118,8 @@ lbmp_status lbmp_batch_permeability(lbmp_batch *b, double *k_g, double *u_mean) 
   try {
     if (!b) return bfail(LBMP_EINVAL, "NULL batch");
     if (!all_fields(b)) return bfail(LBMP_ESTATE, "every instance needs its fields");
-    BCK(cudaSetDevice(b->device));
+    const DeviceScope device_scope(b->device);
+    BCK(device_scope.err);
     cudaError_t e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1161,7 +1167,8 @@ lbmp_status lbmp_batch_populations(lbmp_batch *b, int32_t i, double *f, int32_t 
     if (!b || !f) return bfail(LBMP_EINVAL, "NULL argument");
     if (i < 0 || i >= b->count) return bfail(LBMP_EINVAL, "instance %d out of range", i);
     if (!b->fields_set[i]) return bfail(LBMP_ESTATE, "instance %d has no fields", i);
-    BCK(cudaSetDevice(b->device));
+    const DeviceScope device_scope(b->device);
+    BCK(device_scope.err);
     const BatchInst &I = b->h_inst[i];
     lbmp::StepArgs a = I.a;
     a.y0 = 0;
@@ -1191,7 +1198,8 @@ lbmp_status lbmp_batch_tune(lbmp_batch *b, int32_t steps, int32_t *chosen, doubl
     if (!b) return bfail(LBMP_EINVAL, "NULL batch");
     if (steps < 1) return bfail(LBMP_EINVAL, "steps must be >= 1");
     if (!all_fields(b)) return bfail(LBMP_ESTATE, "every instance needs its fields");
-    BCK(cudaSetDevice(b->device));
+    const DeviceScope device_scope(b->device);
+    BCK(device_scope.err);
     const size_t elem = b->p.storage == LBMP_STORE_FP32 ? 4 : 2;
     // save the current populations and the counter of every instance
     std::vector<void *> saved(b->count, nullptr);

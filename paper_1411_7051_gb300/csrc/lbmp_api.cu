@@ -17,6 +17,7 @@
 #include "lbmp.h"
 #include "kernels.h"
 #include "context.h"
+#include "device_scope.h"
 #include "nvtx_range.h"
 
 using lbmp::StepArgs;
@@ -95,9 +96,7 @@ void free_graphs(lbmp_ctx *c) {
 
 void release(lbmp_ctx *c) {
   if (!c) return;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(c->device);
+  const DeviceScope device_scope(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_graphs(c);
   cudaFree(c->buf[0]);
@@ -114,13 +113,11 @@ void release(lbmp_ctx *c) {
   if (c->h_results) cudaFreeHost(c->h_results);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-  if (prev >= 0) cudaSetDevice(prev);
   delete c;
 }
 
-lbmp_status set_device(lbmp_ctx *c) {
-  LBMP_CK(cudaSetDevice(c->device));
-  return LBMP_OK;
+lbmp_status scope_status(const DeviceScope &d) {
+  return d.err == cudaSuccess ? LBMP_OK : cuda_fail(d.err, "cudaSetDevice");
 }
 
 // Device scratch for caller pointers that live on the host.
@@ -442,7 +439,8 @@ lbmp_status lbmp_set_fields(lbmp_ctx *c, const double *eps, const double *k_i,
   try {
     if (!c || !eps || !k_i || !kn) return fail(LBMP_EINVAL, "lbmp_set_fields: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     const lbmp_params &p = c->p;
     const size_t n = (size_t)p.nx * p.ny;
@@ -555,7 +553,8 @@ lbmp_status lbmp_step(lbmp_ctx *c, int64_t n) {
     if (n < 0) return fail(LBMP_EINVAL, "lbmp_step: n must be >= 0");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_step: call lbmp_set_fields first");
     if (n == 0) return LBMP_OK;
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     // n = 32 q + sum of binary digits: q replays of the 32-step graph, then
     // one replay of each smaller power of two
@@ -583,7 +582,8 @@ lbmp_status lbmp_step(lbmp_ctx *c, int64_t n) {
 lbmp_status lbmp_synchronize(lbmp_ctx *c) {
   const lbmp::NvtxRange nvtx_range("lbmp_synchronize");
   if (!c) return fail(LBMP_EINVAL, "lbmp_synchronize: NULL context");
-  lbmp_status st = set_device(c);
+  const DeviceScope device_scope(c->device);
+  lbmp_status st = scope_status(device_scope);
   if (st) return st;
   LBMP_CK(cudaStreamSynchronize(c->stream));
   return check_err(c);
@@ -596,7 +596,8 @@ lbmp_status lbmp_macroscopic(lbmp_ctx *c, double *rho, double *ux, double *uy,
     if (!c) return fail(LBMP_EINVAL, "lbmp_macroscopic: NULL context");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_macroscopic: no fields set");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     const size_t n = (size_t)c->p.nx * c->p.ny;
     lbmp::MacroOut o{};
@@ -633,7 +634,8 @@ lbmp_status lbmp_apparent_permeability(lbmp_ctx *c, double *ka, int32_t where) {
     if (!c || !ka) return fail(LBMP_EINVAL, "lbmp_apparent_permeability: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_apparent_permeability: no fields set");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     const size_t n = (size_t)c->p.nx * c->p.ny;
     DevTemp tmp;
@@ -661,7 +663,8 @@ lbmp_status lbmp_populations(lbmp_ctx *c, double *f, int32_t where) {
     if (!c || !f) return fail(LBMP_EINVAL, "lbmp_populations: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_populations: no fields set");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     const size_t n = (size_t)c->p.nx * c->p.ny * 9;
     lbmp::MacroOut o{};
@@ -689,7 +692,8 @@ lbmp_status lbmp_set_populations(lbmp_ctx *c, const double *f, int32_t where) {
     if (!c || !f) return fail(LBMP_EINVAL, "lbmp_set_populations: NULL argument");
     if (!valid_where(where)) return fail(LBMP_EINVAL, "where must be LBMP_HOST or LBMP_DEVICE");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_set_populations: no fields set");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     const size_t n = (size_t)c->p.nx * c->p.ny * 9;
     const double *src = f;
@@ -715,7 +719,8 @@ lbmp_status lbmp_permeability(lbmp_ctx *c, double *k_g, double *u_mean) {
   try {
     if (!c) return fail(LBMP_EINVAL, "lbmp_permeability: NULL context");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_permeability: no fields set");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     lbmp::MacroOut o{};
     st = run_macro(c, o, true);
@@ -742,7 +747,8 @@ lbmp_status lbmp_velocity_histogram(lbmp_ctx *c, int32_t nbins, double *umax,
     if (nbins < 1 || nbins > lbmp::kMaxHistBins)
       return fail(LBMP_EINVAL, "nbins must be in [1, %d]", lbmp::kMaxHistBins);
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_velocity_histogram: no fields set");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     if (!c->d_hist) {
       st = dalloc(c, (void **)&c->d_hist, lbmp::kMaxHistBins * sizeof(unsigned long long),
@@ -784,7 +790,8 @@ lbmp_status lbmp_residual(lbmp_ctx *c, double *r) {
   try {
     if (!c || !r) return fail(LBMP_EINVAL, "lbmp_residual: NULL argument");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_residual: no fields set");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     lbmp::MacroOut o{};
     o.uprev = c->uprev;
@@ -803,7 +810,8 @@ lbmp_status lbmp_mass(lbmp_ctx *c, double *m) {
   try {
     if (!c || !m) return fail(LBMP_EINVAL, "lbmp_mass: NULL argument");
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_mass: no fields set");
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     lbmp::MacroOut o{};
     st = run_macro(c, o, true);
@@ -829,7 +837,8 @@ lbmp_status lbmp_get_state(lbmp_ctx *c, void *buf, size_t bytes, int32_t where) 
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_get_state: no fields set");
     size_t need = sizeof(StateHeader) + c->buf_bytes();
     if (bytes < need) return fail(LBMP_EINVAL, "lbmp_get_state: buffer of %zu bytes, need %zu", bytes, need);
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     StateHeader h{};
     h.magic = kStateMagic;
@@ -860,7 +869,8 @@ lbmp_status lbmp_set_state(lbmp_ctx *c, const void *buf, size_t bytes, int32_t w
     if (!c->fields_set) return fail(LBMP_ESTATE, "lbmp_set_state: set the medium first");
     size_t need = sizeof(StateHeader) + c->buf_bytes();
     if (bytes != need) return fail(LBMP_EINVAL, "lbmp_set_state: %zu bytes, expected %zu", bytes, need);
-    lbmp_status st = set_device(c);
+    const DeviceScope device_scope(c->device);
+    lbmp_status st = scope_status(device_scope);
     if (st) return st;
     StateHeader h{};
     cudaMemcpyKind kh = (where == LBMP_HOST) ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;

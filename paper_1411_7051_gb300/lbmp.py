@@ -306,6 +306,46 @@ class SimConfig:
                       int(self.seed) & (2**64 - 1), stream, float(self.kn_beta))
 
 
+def _context_device(stream) -> int:
+    """The current CUDA device, which the library's context is created on;
+    a caller's stream must belong to it."""
+    torch = _torch()
+    dev = torch.cuda.current_device()
+    if stream is not None and stream.device.index != dev:
+        raise ValueError(f"the stream is on cuda:{stream.device.index}, the current device "
+                         f"(where the context is created) is cuda:{dev}")
+    return dev
+
+
+def _in_field(a, shape, device: int):
+    """(pointer, where, keepalive) for a float64 input of ``shape``; a CUDA
+    tensor must sit on ``device``, the context's: the library's kernels
+    dereference the pointer there."""
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        t = a.detach()
+        if t.is_cuda and t.device.index != device:
+            raise ValueError(f"input on cuda:{t.device.index}, the lattice is on cuda:{device}")
+        if t.dtype != torch.float64:
+            t = t.to(torch.float64)
+        t = t.contiguous()
+        if tuple(t.shape) != tuple(shape):
+            t = t.expand(*shape).contiguous()
+        where = DEVICE if t.is_cuda else HOST
+        return ctypes.c_void_p(t.data_ptr()), where, t
+    arr = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
+    return arr.ctypes.data_as(ctypes.c_void_p), HOST, arr
+
+
+def _out_field(shape, device: int | None):
+    """A float64 output of ``shape``: on CUDA device ``device`` (the
+    context's), or on the host for None."""
+    torch = _torch()
+    dev = torch.device("cuda", device) if device is not None else "cpu"
+    t = torch.empty(shape, dtype=torch.float64, device=dev)
+    return t, ctypes.c_void_p(t.data_ptr()), (DEVICE if device is not None else HOST)
+
+
 class Sim:
     """One lattice (``lbmp_ctx``) on the current CUDA device.
 
@@ -319,6 +359,7 @@ class Sim:
         if not torch.cuda.is_available():
             raise LbmpError(ECUDA, "no CUDA device available")
         self.cfg = cfg
+        self.device = _context_device(stream)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self._params = cfg.to_params(self.stream.cuda_stream)
         h = _VP()
@@ -346,25 +387,10 @@ class Sim:
 
     # -- marshalling helpers
     def _in_field(self, a, shape):
-        """(pointer, where, keepalive) for a float64 input of ``shape``."""
-        torch = _torch()
-        if isinstance(a, torch.Tensor):
-            t = a.detach()
-            if t.dtype != torch.float64:
-                t = t.to(torch.float64)
-            t = t.contiguous()
-            if tuple(t.shape) != tuple(shape):
-                t = t.expand(*shape).contiguous()
-            where = DEVICE if t.is_cuda else HOST
-            return ctypes.c_void_p(t.data_ptr()), where, t
-        arr = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
-        return arr.ctypes.data_as(ctypes.c_void_p), HOST, arr
+        return _in_field(a, shape, self.device)
 
     def _out_field(self, shape, device: bool):
-        torch = _torch()
-        dev = torch.device("cuda", torch.cuda.current_device()) if device else "cpu"
-        t = torch.empty(shape, dtype=torch.float64, device=dev)
-        return t, ctypes.c_void_p(t.data_ptr()), (DEVICE if device else HOST)
+        return _out_field(shape, self.device if device else None)
 
     # -- C ABI calls
     def set_fields(self, eps, k_i, kn):
@@ -375,7 +401,7 @@ class Sim:
         if not (we == wk == wn):
             raise ValueError("eps, k_i and kn must all be on the host or all on the device")
         if we == DEVICE:
-            _torch().cuda.current_stream().synchronize()
+            _torch().cuda.current_stream(self.device).synchronize()
         _check(load().lbmp_set_fields(self._h, pe, pk, pn, we))
 
     def step(self, n: int = 1):
@@ -407,7 +433,7 @@ class Sim:
     def set_populations(self, f):
         pf, w, keep = self._in_field(f, (9, self.ny, self.nx))
         if w == DEVICE:
-            _torch().cuda.current_stream().synchronize()
+            _torch().cuda.current_stream(self.device).synchronize()
         _check(load().lbmp_set_populations(self._h, pf, w))
 
     def permeability(self):
@@ -554,6 +580,7 @@ class Batch:
         self.cfg = cfg
         self.sizes = [(int(nx), int(ny)) for nx, ny in sizes]
         self.count = len(self.sizes)
+        self.device = _context_device(stream)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self._params = cfg.to_params(self.stream.cuda_stream)
         nx = (ctypes.c_int32 * self.count)(*[s[0] for s in self.sizes])
@@ -581,14 +608,13 @@ class Batch:
 
     def set_fields(self, i: int, eps, k_i, kn):
         nx, ny = self.sizes[i]
-        helper = Sim.__new__(Sim)
-        pe, we, ke = Sim._in_field(helper, eps, (ny, nx))
-        pk, wk, kk = Sim._in_field(helper, k_i, (ny, nx))
-        pn, wn, kkn = Sim._in_field(helper, kn, (ny, nx))
+        pe, we, ke = _in_field(eps, (ny, nx), self.device)
+        pk, wk, kk = _in_field(k_i, (ny, nx), self.device)
+        pn, wn, kkn = _in_field(kn, (ny, nx), self.device)
         if not (we == wk == wn):
             raise ValueError("eps, k_i and kn must all be on the host or all on the device")
         if we == DEVICE:
-            _torch().cuda.current_stream().synchronize()
+            _torch().cuda.current_stream(self.device).synchronize()
         _check(load().lbmp_batch_set_fields(self._h, int(i), pe, pk, pn, we))
 
     def step(self, n: int = 1):
@@ -606,11 +632,8 @@ class Batch:
 
     def populations(self, i: int, device: bool = True):
         nx, ny = self.sizes[i]
-        torch = _torch()
-        dev = torch.device("cuda", torch.cuda.current_device()) if device else "cpu"
-        f = torch.empty((9, ny, nx), dtype=torch.float64, device=dev)
-        _check(load().lbmp_batch_populations(self._h, int(i), ctypes.c_void_p(f.data_ptr()),
-                                             DEVICE if device else HOST))
+        f, pf, w = _out_field((9, ny, nx), self.device if device else None)
+        _check(load().lbmp_batch_populations(self._h, int(i), pf, w))
         return f
 
     def tune(self, steps: int = 10):
