@@ -735,12 +735,25 @@ def batch_measure(lbmp, torch, n_media: int, n_kn: int, storage: str, K: int, W:
                 clocks=clk.summary() if clk else None)
 
 
-def batch_roofline(r, K, peak, kind):
-    achieved = r["bpu"] * r["nodes"] / (r["ms"] * 1e-3 / K) / 1e9
+def batch_roofline(r, K, peak, kind, storage):
+    """Roofline of the batched step; `traffic` from the committed ncu figures
+    when they were taken on the current batched-kernel sources and on the
+    same set of instances (the same node count)."""
+    from paper_1411_7051_gb300 import build as lbuild
+    per_launch_s = r["ms"] * 1e-3 / K
+    achieved = r["bpu"] * r["nodes"] / per_launch_s / 1e9
+    tr = None
+    if r["staged"]:
+        tr = profiled_traffic(f"batch_{storage}", lbuild.kernel_hash(lbuild.BATCH_KERNEL_FILES))
+        if tr and tr.get("nodes") != r["nodes"]:
+            tr = None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": f"of {kind}",
             "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
-            "bytes_per_update": r["bpu"], "traffic": None,
+            "bytes_per_update": r["bpu"],
+            "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+            "traffic_per_update": (tr["dram_bytes_per_launch"] / r["nodes"] if tr else None),
+            "achieved_dram": (tr["dram_bytes_per_launch"] / per_launch_s / 1e9 if tr else None),
             "kernel": ("lbmp::batch_staged_kernel" if r["staged"] else "lbmp::batch_step_kernel")}
 
 
@@ -761,7 +774,7 @@ def batch_object(lbmp, torch, args):
         out[st] = {"value": r["nodes"] * K / (r["ms"] * 1e-3) / 1e9, "unit": "GLUPS",
                    "ms_per_step": r["ms"] / K, "instances": r["instances"], "nodes": r["nodes"],
                    "shape": r["shape"], "tuned_shape_index": r["chosen"],
-                   "roofline": batch_roofline(r, K, peak, kind), "gpu_launches": r["launches"],
+                   "roofline": batch_roofline(r, K, peak, kind, st), "gpu_launches": r["launches"],
                    "k_g_range": r["k_g_range"], "setup_s": r["setup_s"]}
     return out
 
@@ -792,7 +805,7 @@ def run_batch(args, ws, rank, local):
                        "shape": r["shape"], "l2": "inputs larger than L2, no flush",
                        "timing": f"median of {REPEATS} timed regions of K steps, CUDA events"},
             "ms_per_step_samples": [t / K for t in r["ms_samples"]],
-            "roofline": batch_roofline(r, K, peak, kind),
+            "roofline": batch_roofline(r, K, peak, kind, storage),
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "setup_s": r["setup_s"], "tuned_shape_index": r["chosen"],
             "tune_ms_per_step": r["tune_ms"], "k_g_range": r["k_g_range"],

@@ -46,6 +46,7 @@ def source_hash() -> str:
 
 STEP_KERNEL_FILES = ["kernels.cu", "kernels.h", "lattice.cuh", "staged.cuh"]
 ADJOINT_KERNEL_FILES = ["adjoint.cu", "kernels.h", "lattice.cuh"]
+BATCH_KERNEL_FILES = ["batch.cu", "kernels.h", "lattice.cuh", "staged.cuh"]
 
 
 def kernel_hash(files=STEP_KERNEL_FILES) -> str:

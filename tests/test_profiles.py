@@ -19,7 +19,9 @@ def _traffic():
 
 @pytest.mark.parametrize("tag,files", [("StoreF32", build.STEP_KERNEL_FILES),
                                        ("StoreF16", build.STEP_KERNEL_FILES),
-                                       ("adjoint", build.ADJOINT_KERNEL_FILES)])
+                                       ("adjoint", build.ADJOINT_KERNEL_FILES),
+                                       ("batch_fp16", build.BATCH_KERNEL_FILES),
+                                       ("batch_fp32", build.BATCH_KERNEL_FILES)])
 def test_traffic_matches_the_kernel_sources(tag, files):
     e = _traffic()[tag]
     assert e["source_hash"] == build.kernel_hash(files), (
@@ -31,9 +33,11 @@ def test_traffic_matches_the_kernel_sources(tag, files):
 def test_traffic_per_update_is_plausible():
     """DRAM bytes a lattice update against the algorithmic bytes (80 B FP32,
     44 B FP16, 109.5 B for the adjoint's reverse step): below them only by
-    what the 129 MB L2 can hold back, never far above (re-reads)."""
+    what the 129 MB L2 can hold back, never far above (re-reads; the
+    batched instances 512 and 1024 wide read their row padding too)."""
     t = _traffic()
-    for tag, algo in (("StoreF32", 80.0), ("StoreF16", 44.0), ("adjoint", 109.5)):
+    for tag, algo in (("StoreF32", 80.0), ("StoreF16", 44.0), ("adjoint", 109.5),
+                      ("batch_fp16", 44.0), ("batch_fp32", 80.0)):
         per = t[tag]["dram_bytes_per_launch"] / t[tag]["nodes"]
         held = 129e6 / t[tag]["nodes"]
         assert algo - held - 1.0 <= per <= algo * 1.05, (tag, per)
