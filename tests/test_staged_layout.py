@@ -48,6 +48,13 @@ def stage_cfg(kind="single"):
     return out
 
 
+def batch_pitch_of(nx):
+    """Row pitch of a batched instance (batch.cu: no skew)."""
+    text = open(os.path.join(CSRC, "batch.cu")).read()
+    align = int(re.search(r"kBatchPitchAlign = (\d+);", text).group(1))
+    return ((nx + align - 1) // align) * align
+
+
 def pitch_of(nx):
     text = open(os.path.join(CSRC, "kernels.h")).read()
     align = int(re.search(r"kPitchAlign = (\d+);", text).group(1))
@@ -71,7 +78,7 @@ def replay(nx, ny, walls, store, grids=(1, 7, 152), kind="single"):
     assert bar_bytes + NS * stage_bytes + NS * c["head"] <= 227 * 1024
     assert (bar_bytes + NS * stage_bytes) % 16 == 0  # the batched tile headers follow
     assert 2 * NS * 8 <= bar_bytes
-    pitch = pitch_of(nx)
+    pitch = batch_pitch_of(nx) if kind == "batch" else pitch_of(nx)
     NP = pitch * ny                      # nodes of a plane (the wrap length)
     stride = NP                          # plane stride
     y0, rows = (1, ny - 2) if walls else (0, ny)
