@@ -41,3 +41,21 @@ def test_traffic_per_update_is_plausible():
         per = t[tag]["dram_bytes_per_launch"] / t[tag]["nodes"]
         held = 129e6 / t[tag]["nodes"]
         assert algo - held - 1.0 <= per <= algo * 1.05, (tag, per)
+
+
+def test_bench_reports_batch_traffic_only_for_the_captured_instances():
+    """bench.py's batch roofline takes the committed traffic for the instance
+    set it was captured on (same node count) and reports null otherwise, and
+    never for the non-staged shapes."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    e = _traffic()["batch_fp16"]
+    r = dict(ms=0.71 * 300, nodes=e["nodes"], bpu=44.0, staged=True)
+    roof = bench.batch_roofline(r, 300, 6795.8, "measured", "fp16")
+    assert roof["traffic"] == e["dram_bytes_per_launch"]
+    assert roof["traffic_per_update"] == pytest.approx(e["dram_bytes_per_launch"] / e["nodes"])
+    assert bench.batch_roofline(dict(r, nodes=e["nodes"] + 1), 300, 6795.8, "measured",
+                                "fp16")["traffic"] is None
+    assert bench.batch_roofline(dict(r, staged=False), 300, 6795.8, "measured",
+                                "fp16")["traffic"] is None
