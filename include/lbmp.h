@@ -325,6 +325,8 @@ typedef struct lbmp_batch_info {
  * allocate all instances.  Errors: EINVAL, ENOMEM, ECUDA. */
 lbmp_status lbmp_batch_create(const lbmp_params *p, int32_t count, const int32_t *nx,
                               const int32_t *ny, lbmp_batch **out);
+/* Wait for the batch's queued work and free every resource it holds.  NULL
+ * is accepted.  Always LBMP_OK. */
 lbmp_status lbmp_batch_destroy(lbmp_batch *b);
 /* Medium of instance i ([ny_i][nx_i] float64, as lbmp_set_fields), restart
  * it from rest. */
@@ -368,6 +370,10 @@ lbmp_status lbmp_batch_class(const lbmp_params *p, int32_t count, const int32_t 
  * lbmp_batch_tune reports them; the last one is the staged bulk-copy
  * kernel).  Errors: EINVAL. */
 lbmp_status lbmp_batch_set_shape(lbmp_batch *b, int32_t shape);
+/* Fill *out (host) with the batch's instance count, launch shape, lattice
+ * updates per step, steps and launches so far, device bytes held and
+ * algorithmic bytes per update.  Host-side values; no synchronisation.
+ * Errors: EINVAL (NULL argument). */
 lbmp_status lbmp_batch_get_info(lbmp_batch *b, lbmp_batch_info *out);
 
 /* Global permeability of a lattice state held entirely in caller memory,

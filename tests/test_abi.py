@@ -21,6 +21,18 @@ def test_exports_every_declared_function(L):
         assert hasattr(L, n), f"{n} declared in include/lbmp.h but not exported"
 
 
+def test_every_declaration_is_documented():
+    """Each function include/lbmp.h declares is preceded by its own comment
+    (what it computes, its arguments' meaning and layout, ownership, errors)."""
+    import re
+    with open(lbmp.HEADER) as fh:
+        lines = fh.read().splitlines()
+    for name in lbmp.header_functions():
+        i = next(k for k, l in enumerate(lines)
+                 if re.search(r"\b%s\s*\(" % name, l) and not l.lstrip().startswith(("*", "/*")))
+        assert lines[i - 1].rstrip().endswith("*/"), f"{name} has no comment of its own"
+
+
 def test_fc_host_function(L, orc):
     # library's host f_c against the oracle's (Eq. 6-7)
     for kn in (0.0, 1e-6, 1e-3, 0.1, 0.339, 1.0, 9.16, 10.0, 1e4):
